@@ -1,0 +1,297 @@
+/*
+ * RSOS oracle: plain, slow CPU reference of the (2+1)-d restricted
+ * solid-on-solid growth dynamics of Kelling, Odor & Gemming (arXiv:1605.02620).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may link, load or call
+ * this file: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+ * leg use it.  It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (paper section II and Eq. 6):
+ *   - heights h(x,y) of an L x L periodic square lattice, flat start h = 0;
+ *   - a deposition attempt at site x does h(x) -> h(x)+1 and is accepted only
+ *     if afterwards |h(x) - h(n)| <= N for all four nearest neighbours n
+ *     (Eq. 6).  Given the constraint already holds, this is "accept iff
+ *     h(x) - h(n) < N for every neighbour n";
+ *   - double tiling (DT) domain decomposition (section II): the lattice is cut
+ *     into Tx x Ty tiles, each tile into 2 x 2 sub-tiles, giving four sets of
+ *     sub-tiles that are updated one set after another; the tiling origin is
+ *     moved randomly after every sweep;
+ *   - multisurface coding (section II): the surfaces ("lanes") of one job share
+ *     the sequence of selected sites; each lane takes part in a selection only
+ *     if its own random mask bit is set ("updating only half of the selected
+ *     lattice sites in each attempt");
+ *   - a true random-sequential (RS) reference dynamics: L^2 attempts at
+ *     uniformly chosen sites per Monte-Carlo step;
+ *   - exact sums of h and h^2 per lane, from which the squared interface width
+ *     W^2 = <h^2> - <h>^2 follows (Eq. 2).
+ *
+ * Randomness: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11), written here from that publication.
+ * The counter layout is this project's stream specification (the paper does
+ * not publish one; its RNG is unnamed): key = seed, and
+ *   control draw of sweep t : ctr = (0,       t, 0,      1<<30)
+ *   site draws              : ctr = (tile_id, t, i>>3,   2<<30 | p<<28)
+ *   mask draws              : ctr = (tile_id, t, i>>2,   3<<30 | p<<28 | w)
+ *   RS site draws           : ctr = (a>>2,    s, lane,   0)
+ * with t the sweep index, p the phase, i the selection index inside a
+ * sub-tile activation, w = lane>>5 the 32-lane word of the lane and a the
+ * attempt index inside RS step s.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox-4x32-10 (Salmon et al. 2011, section 4.2: the Philox S-box is a     */
+/* pair of 32x32->64 multiplications whose high halves are XORed with the     */
+/* other counter words and the round key; the key is advanced by a Weyl      */
+/* sequence between rounds).                                                  */
+/* ------------------------------------------------------------------------- */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u /* floor(2^32 * (golden ratio - 1)) */
+#define ORC_PHILOX_W1 0xBB67AE85u /* floor(2^32 * (sqrt(3) - 1))      */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * x0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += ORC_PHILOX_W0;
+        k1 += ORC_PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The four Philox constants (M0, M1, W0, W1), for the constant tests. */
+void orc_philox_constants(uint32_t out[4])
+{
+    out[0] = ORC_PHILOX_M0; out[1] = ORC_PHILOX_M1;
+    out[2] = ORC_PHILOX_W0; out[3] = ORC_PHILOX_W1;
+}
+
+/* n consecutive blocks: counter word 0 (carrying into word 1) runs from ctr0. */
+void orc_philox_bulk(const uint32_t ctr0[4], const uint32_t key[2], uint64_t n, uint32_t* out)
+{
+    uint64_t base = ((uint64_t)ctr0[1] << 32) | ctr0[0];
+    for (uint64_t b = 0; b < n; ++b) {
+        uint64_t c01 = base + b;
+        uint32_t c[4] = {(uint32_t)c01, (uint32_t)(c01 >> 32), ctr0[2], ctr0[3]};
+        orc_philox4x32_10(c, key, out + 4 * b);
+    }
+}
+
+/* floor(r * n / 2^32): maps a uniform 32-bit word onto [0, n). */
+static uint32_t orc_mulhi32(uint32_t r, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)r * (uint64_t)n) >> 32);
+}
+
+/* The 24 permutations of (0,1,2,3) in lexicographic order. */
+static void orc_permutation(uint32_t index, int perm[4])
+{
+    int pool[4] = {0, 1, 2, 3};
+    int n = 4;
+    uint32_t fact[4] = {6, 2, 1, 1};
+    for (int pos = 0; pos < 4; ++pos) {
+        uint32_t pick = index / fact[pos];
+        index %= fact[pos];
+        perm[pos] = pool[pick];
+        for (int m = (int)pick; m < n - 1; ++m) pool[m] = pool[m + 1];
+        --n;
+    }
+}
+
+typedef struct {
+    int32_t L;           /* periodic lattice edge                              */
+    int32_t N;           /* step bound of Eq. 6                                */
+    int32_t Tx, Ty;      /* DT tile edges (even), L % Tx == 0 and L % Ty == 0  */
+    int32_t phase_order; /* 0: random permutation per sweep, 1: fixed 0,1,2,3  */
+    int32_t pad_;
+    uint64_t seed;       /* Philox key                                         */
+} orc_params;
+
+/* Control draw of sweep t: origin of the tiling and order of the four
+ * sub-tile sets (section II: "the origin of the DD was moved randomly"). */
+void orc_control(const orc_params* P, uint64_t t, int32_t* ox, int32_t* oy, int32_t perm[4])
+{
+    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    uint32_t ctr[4] = {0u, (uint32_t)t, 0u, 1u << 30};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    *ox = (int32_t)orc_mulhi32(r[0], (uint32_t)P->Tx);
+    *oy = (int32_t)orc_mulhi32(r[1], (uint32_t)P->Ty);
+    if (P->phase_order == 1) {
+        for (int m = 0; m < 4; ++m) perm[m] = m;
+    } else {
+        orc_permutation(orc_mulhi32(r[2], 24u), perm);
+    }
+}
+
+static int64_t* orc_at(int64_t* h, int32_t L, int32_t x, int32_t y)
+{
+    return &h[(int64_t)y * L + x];
+}
+
+/* One attempt at (x, y): Eq. 6.  Returns 1 if the deposit was accepted. */
+static int orc_attempt(int64_t* h, int32_t L, int32_t N, int32_t x, int32_t y)
+{
+    int32_t xe = (x + 1) % L, xw = (x + L - 1) % L;
+    int32_t yn = (y + L - 1) % L, ys = (y + 1) % L;
+    int64_t hx = *orc_at(h, L, x, y);
+    int64_t nb[4] = {*orc_at(h, L, xe, y), *orc_at(h, L, xw, y),
+                     *orc_at(h, L, x, yn), *orc_at(h, L, x, ys)};
+    for (int m = 0; m < 4; ++m) {
+        int64_t after = hx + 1 - nb[m];
+        if (after > N || after < -N) return 0;
+    }
+    *orc_at(h, L, x, y) = hx + 1;
+    return 1;
+}
+
+/* One DT sweep (sweep index t) of a single lane.  Returns accepted deposits. */
+static int64_t orc_dt_sweep_lane(const orc_params* P, int64_t* h, uint32_t lane, uint64_t t)
+{
+    const int32_t L = P->L, Tx = P->Tx, Ty = P->Ty;
+    const int32_t sx = Tx / 2, sy = Ty / 2;
+    const uint32_t a = (uint32_t)(sx * sy);
+    const int32_t ntx = L / Tx, nty = L / Ty;
+    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    int32_t ox, oy, perm[4];
+    int64_t accepted = 0;
+    orc_control(P, t, &ox, &oy, perm);
+    for (int p = 0; p < 4; ++p) {
+        const int q = perm[p];
+        const int32_t qx = q & 1, qy = q >> 1;
+        for (int32_t ty = 0; ty < nty; ++ty) {
+            for (int32_t tx = 0; tx < ntx; ++tx) {
+                const uint32_t tile_id = (uint32_t)(ty * ntx + tx);
+                uint32_t site_r[4], mask_r[4];
+                for (uint32_t i = 0; i < 2u * a; ++i) {
+                    if ((i & 7u) == 0) {
+                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 3, (2u << 30) | ((uint32_t)p << 28)};
+                        orc_philox4x32_10(c, key, site_r);
+                    }
+                    if ((i & 3u) == 0) {
+                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 2,
+                                         (3u << 30) | ((uint32_t)p << 28) | (lane >> 5)};
+                        orc_philox4x32_10(c, key, mask_r);
+                    }
+                    uint32_t word = site_r[(i >> 1) & 3u];
+                    uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
+                    uint32_t k = (half * a) >> 16;
+                    uint32_t bit = (mask_r[i & 3u] >> (lane & 31u)) & 1u;
+                    if (!bit) continue;
+                    int32_t u = qx * sx + (int32_t)(k % (uint32_t)sx);
+                    int32_t v = qy * sy + (int32_t)(k / (uint32_t)sx);
+                    int32_t x = (ox + tx * Tx + u) % L;
+                    int32_t y = (oy + ty * Ty + v) % L;
+                    accepted += orc_attempt(h, L, P->N, x, y);
+                }
+            }
+        }
+    }
+    return accepted;
+}
+
+/* One random-sequential Monte-Carlo step (L^2 attempts) of a single lane. */
+static int64_t orc_rs_step_lane(const orc_params* P, int64_t* h, uint32_t lane, uint64_t s)
+{
+    const int32_t L = P->L;
+    const uint32_t area = (uint32_t)L * (uint32_t)L;
+    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    uint32_t r[4];
+    int64_t accepted = 0;
+    for (uint32_t at = 0; at < area; ++at) {
+        if ((at & 3u) == 0) {
+            uint32_t c[4] = {at >> 2, (uint32_t)s, lane, 0u};
+            orc_philox4x32_10(c, key, r);
+        }
+        uint32_t site = orc_mulhi32(r[at & 3u], area);
+        accepted += orc_attempt(h, L, P->N, (int32_t)(site % (uint32_t)L), (int32_t)(site / (uint32_t)L));
+    }
+    return accepted;
+}
+
+/*
+ * Advance n_lanes independent height fields by n_sweeps sweeps, starting at
+ * sweep index t0.  h is [n_lanes][L][L] int64 (row-major, x fastest); lanes[m]
+ * is the lane index j of field m (it selects the mask bit and mask word).
+ * rs != 0 selects the random-sequential dynamics instead of DT.
+ * accepted (nullable) receives the accepted deposits per field.
+ * Lanes are independent simulations; they run in parallel threads.
+ */
+int orc_sweeps(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n_lanes,
+               uint64_t t0, uint64_t n_sweeps, int32_t rs, int32_t n_threads, int64_t* accepted)
+{
+    if (P->L < 1 || P->N < 1 || n_lanes < 0) return -1;
+    if (!rs) {
+        if (P->Tx < 2 || P->Ty < 2 || (P->Tx & 1) || (P->Ty & 1)) return -1;
+        if (P->L % P->Tx || P->L % P->Ty) return -1;
+    }
+    const int64_t area = (int64_t)P->L * P->L;
+    if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+    for (int32_t m = 0; m < n_lanes; ++m) {
+        int64_t acc = 0;
+        for (uint64_t t = t0; t < t0 + n_sweeps; ++t) {
+            acc += rs ? orc_rs_step_lane(P, h + m * area, lanes[m], t)
+                      : orc_dt_sweep_lane(P, h + m * area, lanes[m], t);
+        }
+        if (accepted) accepted[m] = acc;
+    }
+    return 0;
+}
+
+/*
+ * Exact sums of h and h^2 per field (Eq. 2 numerators), accumulated in
+ * 128-bit integers.  sum_h2 is returned as (hi, lo) 64-bit halves of the
+ * signed 128-bit value.
+ */
+void orc_sums(const int64_t* h, int32_t L, int32_t n_lanes, int64_t* sum_h,
+              int64_t* sum_h2_hi, uint64_t* sum_h2_lo)
+{
+    const int64_t area = (int64_t)L * L;
+    for (int32_t m = 0; m < n_lanes; ++m) {
+        __int128 s1 = 0, s2 = 0;
+        for (int64_t k = 0; k < area; ++k) {
+            __int128 v = h[m * area + k];
+            s1 += v;
+            s2 += v * v;
+        }
+        sum_h[m] = (int64_t)s1;
+        sum_h2_hi[m] = (int64_t)(s2 >> 64);
+        sum_h2_lo[m] = (uint64_t)s2;
+    }
+}
+
+/* Largest |h(x) - h(n)| over all nearest-neighbour pairs of each field. */
+void orc_max_step(const int64_t* h, int32_t L, int32_t n_lanes, int64_t* out)
+{
+    const int64_t area = (int64_t)L * L;
+    for (int32_t m = 0; m < n_lanes; ++m) {
+        const int64_t* f = h + m * area;
+        int64_t best = 0;
+        for (int32_t y = 0; y < L; ++y) {
+            for (int32_t x = 0; x < L; ++x) {
+                int64_t v = f[(int64_t)y * L + x];
+                int64_t de = v - f[(int64_t)y * L + (x + 1) % L];
+                int64_t ds = v - f[(int64_t)((y + 1) % L) * L + x];
+                if (de < 0) de = -de;
+                if (ds < 0) ds = -ds;
+                if (de > best) best = de;
+                if (ds > best) best = ds;
+            }
+        }
+        out[m] = best;
+    }
+}

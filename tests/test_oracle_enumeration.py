@@ -1,0 +1,89 @@
+"""Long oracle runs against exact Markov-chain enumeration (tiny lattices).
+
+The stationary growth velocity v (height gain per site per sweep) and the
+stationary squared width E[W^2] (Eq. 2) of the RS and DT dynamics are
+computed exactly by ``oracle/enumerate.py`` (stored in
+tests/golden/enumeration.json by tests/golden/make_enumeration.py).  Long
+oracle simulations must reproduce them within their statistical error, taken
+across independent seeds because lanes of one job share the selected sites.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import enumerate as en
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "enumeration.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _simulate(L, N, T, order, rs, n_seeds, n_lanes, burn, blocks, block_len):
+    v_seed, w_seed = [], []
+    for seed in range(n_seeds):
+        p = O.Params(L=L, N=N, Tx=T, Ty=T, phase_order=order, seed=7919 * seed + 13)
+        lanes = list(range(n_lanes))
+        h = O.flat(L, n_lanes)
+        O.sweeps(p, h, lanes, 0, burn, rs=rs)
+        s_start, _ = O.sums(h)
+        t = burn
+        w2 = []
+        for _ in range(blocks):
+            O.sweeps(p, h, lanes, t, block_len, rs=rs)
+            t += block_len
+            s1, s2 = O.sums(h)
+            w2.append(np.mean([O.width2(a, b, L) for a, b in zip(s1, s2)]))
+        s_end, _ = O.sums(h)
+        v_seed.append(np.mean([(b - a) / (L * L * (t - burn)) for a, b in zip(s_start, s_end)]))
+        w_seed.append(np.mean(w2))
+    v_seed, w_seed = np.array(v_seed), np.array(w_seed)
+    n = len(v_seed)
+    return v_seed.mean(), v_seed.std(ddof=1) / math.sqrt(n), w_seed.mean(), w_seed.std(ddof=1) / math.sqrt(n)
+
+
+def test_golden_file_reproduces():
+    g = _golden()
+    fresh = {(c["L"], c["N"]): c for c in [en.rs_chain(2, 1), en.rs_chain(3, 1)]}
+    for c in g["rs"]:
+        if (c["L"], c["N"]) in fresh:
+            assert c["velocity"] == pytest.approx(fresh[(c["L"], c["N"])]["velocity"], abs=1e-12)
+            assert c["w2"] == pytest.approx(fresh[(c["L"], c["N"])]["w2"], abs=1e-12)
+    d = en.dt_chain(2, 1, 2, 2, 0)
+    c = next(c for c in g["dt"] if (c["L"], c["N"], c["Tx"], c["phase_order"]) == (2, 1, 2, 0))
+    assert c["velocity"] == pytest.approx(d["velocity"], abs=1e-12)
+    # velocity of RS at L = 2, N = 1 is the rational 24/47
+    c = next(c for c in g["rs"] if (c["L"], c["N"]) == (2, 1))
+    assert c["velocity"] == pytest.approx(24 / 47, abs=1e-12)
+
+
+def _cases():
+    g = _golden()
+    out = []
+    for c in g["rs"]:
+        out.append(pytest.param(c, True, id=f"rs-L{c['L']}-N{c['N']}"))
+    for c in g["dt"]:
+        out.append(pytest.param(c, False, id=f"dt-L{c['L']}-N{c['N']}-T{c['Tx']}-o{c['phase_order']}"))
+    return out
+
+
+@pytest.mark.parametrize("case,rs", _cases())
+def test_long_runs_match_exact_chain(case, rs):
+    L, N = case["L"], case["N"]
+    T = case.get("Tx", 2)
+    order = case.get("phase_order", 0)
+    if L == 2:
+        args = dict(n_seeds=24, n_lanes=16, burn=200, blocks=40, block_len=100)
+    elif L == 3:
+        args = dict(n_seeds=16, n_lanes=8, burn=300, blocks=40, block_len=50)
+    else:
+        args = dict(n_seeds=16, n_lanes=8, burn=300, blocks=30, block_len=50)
+    v, dv, w, dw = _simulate(L, N, T, order, rs, **args)
+    assert abs(v - case["velocity"]) < 4.5 * dv + 1e-9, (v, dv, case["velocity"])
+    assert abs(w - case["w2"]) < 4.5 * dw + 1e-9, (w, dw, case["w2"])
