@@ -1,0 +1,313 @@
+"""Benchmark: RSOS site-update attempts/s on one GB300 (per GPU of a node).
+
+One step is one whole multisurface job through the C ABI: flat init, 10^4
+double-tiling sweeps of an L = 4096 periodic lattice with N = 1 and 64
+surfaces in uint64 words (8x8 tiles, seed = 0 + rank), exact sum h / sum h^2
+at 40 log-spaced times, and the read-back of the W^2 series.  value =
+L^2 * S * sweeps / time (expected attempts, one sweep = 1 MCS).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the reference arm of this project:
+there is no reference code, only the paper) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RSOS site-update attempts/s on 1 GB300 (plain vs batched); % HBM roofline"
+WORKLOAD = dict(workload="ms-n1: L=4096 periodic, N=1, 64 surfaces bit-sliced in uint64 words, 8x8 DT tiles, "
+                         "flat start, 1e4 sweeps, W^2 per surface at 40 log-spaced times",
+                L=4096, N=1, surfaces=64, tile=8, sweeps=10000, measurements=40)
+KERNEL_SOURCES = ["paper_1605_02620_gb300/csrc/rsos_device.cuh", "paper_1605_02620_gb300/csrc/rsos_sweep.cuh",
+                  "paper_1605_02620_gb300/csrc/rsos_logic.cuh", "paper_1605_02620_gb300/csrc/philox.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "phase_kernel_L4096_N1_S64.md")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "of measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def dist_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1605_02620_gb300 as R
+    from paper_1605_02620_gb300.inputs import log_schedule
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    W = WORKLOAD
+    L, S, sweeps = W["L"], W["surfaces"], W["sweeps"]
+    times = log_schedule(sweeps, W["measurements"])
+    seed = rank
+    params = R.rsos_params(L=L, N=W["N"], surfaces=S, tile=W["tile"], seed=seed,
+                           series_capacity=len(times) + 1)
+    nbytes = R.rsos_required_bytes(params)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (buf.data_ptr() + 255) // 256 * 256
+
+    def one_job(device_timed=True):
+        h = R.rsos_init(params, dev_buf=base, dev_bytes=nbytes, stream=stream)
+        R.rsos_schedule(h, times)
+        R.rsos_sweep(h, sweeps, stream=stream)
+        ts, s1, s2, w2 = R.rsos_read_series(h, S, len(times) + 1, stream=stream)
+        R.rsos_free(h)
+        return ts, w2
+
+    for _ in range(args.warmup):
+        one_job()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ts, w2 = one_job()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    dev_ms = dist_max(dev_ms, world)
+
+    # Dominant kernel (the phase kernel), timed alone on the same stream.
+    h = R.rsos_init(params, dev_buf=base, dev_bytes=nbytes, stream=stream)
+    R.rsos_sweep(h, 50, stream=stream)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_kernel_sweeps = 200
+    k0.record(stream)
+    R.rsos_sweep(h, n_kernel_sweeps, stream=stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    R.rsos_free(h)
+    launch_ms = k0.elapsed_time(k1) / (4 * n_kernel_sweeps)
+
+    # End to end through the public API with host buffers: the library
+    # allocates device memory, runs, and the series is copied to host arrays.
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p2 = R.rsos_params(L=L, N=W["N"], surfaces=S, tile=W["tile"], seed=seed, series_capacity=len(times) + 1)
+        h = R.rsos_init(p2, stream=stream)
+        R.rsos_schedule(h, times)
+        R.rsos_sweep(h, sweeps, stream=stream)
+        R.rsos_read_series(h, S, len(times) + 1, stream=stream)
+        R.rsos_free(h)
+    torch.cuda.synchronize()
+    e2e_s = dist_max(time.perf_counter() - t0, world)
+
+    attempts = float(L) * L * S * sweeps
+    value = attempts * world * args.steps / (dev_ms / 1e3)
+    e2e_value = attempts * world * e2e_steps / e2e_s
+    peaks, peak_src = measured_peaks()
+    alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S / 4.0  # per phase launch
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    launches_per_job = 1 + 4 * sweeps + 3 * len(times)
+    if rank != 0:
+        return
+    cpu = cpu_baseline(L, W["N"], W["tile"], seed) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 (bit-sliced int)", "data": "synthetic",
+        "config": dict(W, parallelism=f"replicas{world}", l2="inputs larger than L2 (256 MiB lattice per job)",
+                       seed=seed),
+        "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": (len(times)) * S * 4 * 8 + 8},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
+                     "kernel": "rsos::phase_kernel<1, uint64_t, 4>", "launch_ms": launch_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": launches_per_job * args.steps,
+        "w2_final_mean": float(sum(w2[-1]) / len(w2[-1])),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def rsos_bits(N: int) -> int:
+    return 2 if N <= 1 else (3 if N <= 3 else 4)
+
+
+def cpu_baseline(L, N, T, seed, target_s: float = 12.0):
+    """The oracle, as it stands, on the host cores: one DT sweep of L = 4096 for
+    as many lanes as there are cores (one lane per thread), repeated until
+    about ``target_s`` seconds of CPU work."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    p = O.Params(L=L, N=N, Tx=T, Ty=T, seed=seed)
+    lanes = list(range(cores))
+    h = O.flat(L, cores)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        O.sweeps(p, h, lanes, done, 1, threads=cores)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > target_s or done >= 8:
+            break
+    value = float(L) * L * cores * done / el
+    return {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} DT sweep(s) of L={L}, N={N}, {cores} lanes (one per thread) from the flat start"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    W = WORKLOAD
+    cores = os.cpu_count() or 1
+    L = W["L"]
+    p = O.Params(L=L, N=W["N"], Tx=W["tile"], Ty=W["tile"], seed=0)
+    lanes = list(range(cores))
+    h = O.flat(L, cores)
+    for k in range(args.warmup):
+        O.sweeps(p, h, lanes, k, 1, threads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.sweeps(p, h, lanes, args.warmup + k, 1, threads=cores)
+    el = time.perf_counter() - t0
+    value = float(L) * L * cores * args.steps / el
+    sample = f"{args.steps} DT sweep(s) of L={L}, N={W['N']}, {cores} lanes (one per thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(W, parallelism="host threads", note="each step is one sweep of cores lanes (bounded sample)"),
+        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

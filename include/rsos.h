@@ -1,0 +1,182 @@
+/*
+ * rsos.h -- C ABI of the GB300 RSOS multisurface sweep library (librsos.so).
+ *
+ * Kelling, Odor & Gemming, "Universality of (2+1)-dimensional restricted
+ * solid-on-solid models" (arXiv:1605.02620):
+ *   - model: deposition h -> h+1 at a site, accepted only if every
+ *     nearest-neighbour height difference stays within N (Eq. 6), on a
+ *     periodic L x L lattice from a flat start (section II);
+ *   - many surfaces ("lanes") of one job share the sequence of selected sites
+ *     and each lane acts on a selection only through its own random half mask
+ *     (multisurface coding, section II);
+ *   - double tiling: Tx x Ty tiles, each split into 2 x 2 sub-tiles, four sets
+ *     updated in turn, tiling origin moved randomly after every sweep
+ *     (section II);
+ *   - time in sweeps; one sweep is L^2 expected attempts per surface (1 MCS);
+ *   - observable: squared interface width W^2 = <h^2> - <h>^2 (Eq. 2), at
+ *     measurement times such as those of Eq. 10.
+ * The random stream (Philox-4x32-10 keyed by the seed, counters built from
+ * sweep, phase, tile, selection and lane word) is specified in the library's
+ * design notes; results are a pure function of (params, t).
+ *
+ * Conventions for every call:
+ *   - return value: RSOS_OK (0) or a negative RSOS_E* code; no C++ exception
+ *     ever crosses this boundary;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *   - device memory is owned by the library unless the caller passes its own
+ *     buffer to rsos_init; host arrays are owned by the caller;
+ *   - a handle is not thread-safe; distinct handles are independent;
+ *   - after a CUDA error the handle is poisoned: every later call returns
+ *     RSOS_ECUDA and rsos_last_cuda_error() gives the CUDA code.
+ */
+#ifndef RSOS_H
+#define RSOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSOS_OK 0
+#define RSOS_EINVAL (-1)    /* invalid argument (sizes, ranges, NULL pointers)      */
+#define RSOS_ENOMEM (-2)    /* device allocation failed or caller buffer too small  */
+#define RSOS_ECUDA (-3)     /* a CUDA call failed (sticky for the handle)           */
+#define RSOS_EOVERFLOW (-4) /* a sum does not fit int64 (W^2 is still valid)        */
+#define RSOS_ETIMEOUT (-5)  /* a device-side wait gave up; the GPU stays usable     */
+#define RSOS_EBUSY (-6)     /* the object is in use (e.g. a batch still running)    */
+#define RSOS_ERANGE (-7)    /* capacity exhausted (series full, t limit reached)    */
+
+typedef struct rsos_handle rsos_handle;
+typedef struct rsos_batch rsos_batch;
+
+/* Parameters of one job: S surfaces of one L x L lattice.
+ *   L            periodic edge, L >= Tx, L % tile_x == 0 and L % tile_y == 0.
+ *   N            step bound of Eq. 6, 1 <= N <= 7 (coded in B = ceil(log2(2N+1))
+ *                bits per site and surface).
+ *   surfaces     S >= 1.  S == 1 runs the plain path (int32 heights, lane 0 of
+ *                the stream); S > 1 the multisurface path with ceil(S/32)
+ *                32-lane words per site and bit plane.  Lane j of any job is the
+ *                same surface whatever S is.
+ *   tile_x/y     DT tile edges (section II; 8 x 8 in the paper); the GPU path
+ *                supports square tiles 2, 4, 8 and 16.  Part of the model: they
+ *                change the dynamics.  0 means 8.
+ *   phase_order  0: random permutation of the four sub-tile sets each sweep;
+ *                1: fixed order 0,1,2,3.
+ *   series_capacity  number of measurements the device series buffer holds
+ *                (0 means 1024).
+ *   engine       0 auto, 1 one launch per phase, 2 persistent dataflow kernel.
+ *                Every engine gives bit-identical results.
+ *   seed         Philox key of the job.                                       */
+typedef struct {
+    int32_t L;
+    int32_t N;
+    int32_t surfaces;
+    int32_t tile_x;
+    int32_t tile_y;
+    int32_t phase_order;
+    int32_t series_capacity;
+    int32_t engine;
+    uint64_t seed;
+} rsos_params;
+
+/* Bytes of device memory a job needs (lattice planes, h(0,0) per surface,
+ * measurement scratch, series buffer).  Returns RSOS_EINVAL for invalid
+ * params. */
+int rsos_required_bytes(const rsos_params* params, size_t* bytes);
+
+/* Create a job at time t = 0 with the flat initial condition (section II).
+ *   dev_buf/dev_bytes  NULL/0: the library allocates and later frees the device
+ *                memory; otherwise a caller-owned device buffer of at least
+ *                rsos_required_bytes bytes, 256-byte aligned, that must outlive
+ *                the handle (the library never frees it).
+ *   stream       initialisation kernels are queued on it (asynchronous).
+ *   out          receives the handle (set to NULL on error).                  */
+int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* stream,
+              rsos_handle** out);
+
+/* Queue n_sweeps DT sweeps (t -> t + n_sweeps) on stream; asynchronous.  At
+ * every time in the measurement schedule (rsos_schedule) reached on the way,
+ * exact sums are computed on the device and appended to the series buffer.
+ * RSOS_ERANGE if t would exceed 2^32 - 1 or the series buffer would overflow. */
+int rsos_sweep(rsos_handle* h, int64_t n_sweeps, void* stream);
+
+/* Measure now (time t of the handle) and return per surface, into host
+ * arrays of length S: sum_h = sum h, sum_h2 = sum h^2 (Eq. 2 numerators,
+ * exact), w2 = W^2 (nullable), and *t_out = t (nullable).  Synchronises the
+ * stream.  RSOS_EOVERFLOW if some sum does not fit int64 (then the affected
+ * sums are set to INT64_MIN while w2 stays exact to double rounding). */
+int rsos_width(rsos_handle* h, int64_t* sum_h, int64_t* sum_h2, double* w2, int64_t* t_out,
+               void* stream);
+
+/* Set the measurement schedule: ascending times (completed sweeps, Eq. 10 or
+ * log-spaced); times <= the current t are ignored.  Copies the array.  A time
+ * of 0 on a fresh handle records the flat start. */
+int rsos_schedule(rsos_handle* h, const int64_t* times, int32_t n);
+
+/* Copy the measured series to host arrays: times[cap], sum_h[cap*S],
+ * sum_h2[cap*S], w2[cap*S] (row m = measurement m, column = surface; any of
+ * the last three nullable).  *n_out receives the number of rows written
+ * (min(cap, measurements so far)).  Synchronises the stream.
+ * RSOS_EOVERFLOW as for rsos_width. */
+int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* sum_h2, double* w2,
+                     int32_t cap, int32_t* n_out, void* stream);
+
+/* Absolute heights of one surface at the current time into host_LxL
+ * (row-major, x fastest, int64 [L*L]).  Synchronises the stream. */
+int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream);
+
+/* Current time of the handle (completed sweeps). */
+int rsos_time(const rsos_handle* h, int64_t* t_out);
+
+/* Release the handle and the device memory it allocated.  NULL-safe.
+ * Synchronises the device before freeing. */
+int rsos_free(rsos_handle* h);
+
+/* Static description of a status code. */
+const char* rsos_strerror(int status);
+
+/* CUDA error code behind the last RSOS_ECUDA of the handle (0 if none). */
+int rsos_last_cuda_error(const rsos_handle* h);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent jobs of different L and N advanced together by
+ * one persistent dataflow kernel (captured in a CUDA graph), each to its own
+ * final time.  Jobs never interact; every job's result is bit-identical to the
+ * same job run alone.
+ * ------------------------------------------------------------------------- */
+
+/* Create a batch of n_jobs jobs (params[i], t_max[i] sweeps each) whose device
+ * memory must fit hbm_budget bytes (0 = no limit).  Each job starts flat at
+ * t = 0; its width is measured at t_max (and at the times of its schedule, if
+ * set with rsos_batch_schedule).  RSOS_ENOMEM if the budget is exceeded. */
+int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n_jobs,
+                      size_t hbm_budget, rsos_batch** out);
+
+/* Per-job measurement schedule (ascending times <= t_max[job]); optional. */
+int rsos_batch_schedule(rsos_batch* b, int32_t job, const int64_t* times, int32_t n);
+
+/* Queue the whole batch on stream (asynchronous).  A device wait that exceeds
+ * its time limit ends the launch with RSOS_ETIMEOUT reported by
+ * rsos_batch_poll. */
+int rsos_batch_run(rsos_batch* b, void* stream);
+
+/* Non-blocking: ids of jobs finished since the last poll into done_ids
+ * (capacity cap), count into *n_done.  Returns RSOS_ETIMEOUT if the device
+ * reported a wait that gave up, RSOS_EBUSY while work is in flight and no job
+ * finished, else RSOS_OK. */
+int rsos_batch_poll(rsos_batch* b, int32_t* done_ids, int32_t cap, int32_t* n_done);
+
+/* Handle of job i of the batch (for rsos_width / rsos_read_series /
+ * rsos_heights after the job finished).  Owned by the batch. */
+int rsos_batch_job(rsos_batch* b, int32_t job, rsos_handle** out);
+
+/* Synchronise and release the batch and all its jobs.  NULL-safe. */
+int rsos_batch_free(rsos_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSOS_H */

@@ -1,0 +1,240 @@
+"""GB300-native RSOS multisurface sweep (Kelling, Odor & Gemming, arXiv:1605.02620).
+
+Thin ctypes binding over the C ABI of ``include/rsos.h`` (librsos.so).  Every
+function has the name of the C entry point and only marshals arguments: all
+work runs in the library's CUDA kernels.  There is no CPU fallback; if the
+shared library cannot be loaded (or built from source with nvcc) the first
+call raises.
+
+PyTorch is optional plumbing: a ``torch.cuda.Stream`` (or a raw cudaStream_t
+integer) may be passed wherever a stream is accepted, and a CUDA tensor may be
+passed as the caller-owned device buffer of ``rsos_init``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "RsosError", "rsos_params", "rsos_required_bytes", "rsos_init", "rsos_sweep", "rsos_width",
+    "rsos_schedule", "rsos_read_series", "rsos_heights", "rsos_time", "rsos_free", "rsos_strerror",
+    "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
+    "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "library_path",
+]
+
+RSOS_OK = 0
+RSOS_EINVAL = -1
+RSOS_ENOMEM = -2
+RSOS_ECUDA = -3
+RSOS_EOVERFLOW = -4
+RSOS_ETIMEOUT = -5
+RSOS_EBUSY = -6
+RSOS_ERANGE = -7
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "librsos.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class RsosError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {rsos_strerror(status)} ({status})")
+        self.status = status
+
+
+class rsos_params(ctypes.Structure):
+    """Mirror of the C struct rsos_params (include/rsos.h)."""
+    _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("surfaces", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("phase_order", ctypes.c_int32),
+                ("series_capacity", ctypes.c_int32), ("engine", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+    def __init__(self, L=64, N=1, surfaces=1, tile=8, phase_order=0, series_capacity=0, engine=0, seed=0):
+        super().__init__(int(L), int(N), int(surfaces), int(tile), int(tile), int(phase_order),
+                         int(series_capacity), int(engine), int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        P = ctypes.POINTER
+        sig = {
+            "rsos_required_bytes": [P(rsos_params), P(sz)],
+            "rsos_init": [P(rsos_params), vp, sz, vp, P(vp)],
+            "rsos_sweep": [vp, i64, vp],
+            "rsos_width": [vp, P(i64), P(i64), P(ctypes.c_double), P(i64), vp],
+            "rsos_schedule": [vp, P(i64), i32],
+            "rsos_read_series": [vp, P(i64), P(i64), P(i64), P(ctypes.c_double), i32, P(i32), vp],
+            "rsos_heights": [vp, i32, P(i64), vp],
+            "rsos_time": [vp, P(i64)],
+            "rsos_free": [vp],
+            "rsos_last_cuda_error": [vp],
+            "rsos_batch_create": [P(rsos_params), P(i64), i32, sz, P(vp)],
+            "rsos_batch_schedule": [vp, i32, P(i64), i32],
+            "rsos_batch_run": [vp, vp],
+            "rsos_batch_poll": [vp, P(i32), i32, P(i32)],
+            "rsos_batch_job": [vp, i32, P(vp)],
+            "rsos_batch_free": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.rsos_strerror.argtypes = [ctypes.c_int]
+        lib.rsos_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(int(s.cuda_stream))  # torch.cuda.Stream
+
+
+def _check(rc: int, what: str, allow=()):
+    if rc != RSOS_OK and rc not in allow:
+        raise RsosError(rc, what)
+    return rc
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def rsos_strerror(status: int) -> str:
+    return _load().rsos_strerror(int(status)).decode()
+
+
+def rsos_required_bytes(params: rsos_params) -> int:
+    out = ctypes.c_size_t()
+    _check(_load().rsos_required_bytes(ctypes.byref(params), ctypes.byref(out)), "rsos_required_bytes")
+    return out.value
+
+
+def rsos_init(params: rsos_params, dev_buf=None, dev_bytes: int = 0, stream=None):
+    """Create a job (flat start, t = 0).  ``dev_buf``: None (library allocates),
+    an integer device address, or a CUDA tensor (its storage, which the caller
+    keeps alive).  Returns the opaque handle."""
+    ptr = None
+    if dev_buf is not None:
+        if isinstance(dev_buf, int):
+            ptr = ctypes.c_void_p(dev_buf)
+        else:
+            ptr = ctypes.c_void_p(int(dev_buf.data_ptr()))
+            if not dev_bytes:
+                dev_bytes = int(dev_buf.numel() * dev_buf.element_size())
+    h = ctypes.c_void_p()
+    _check(_load().rsos_init(ctypes.byref(params), ptr, int(dev_bytes), _stream(stream), ctypes.byref(h)),
+           "rsos_init")
+    return h
+
+
+def rsos_sweep(h, n_sweeps: int, stream=None) -> None:
+    _check(_load().rsos_sweep(h, int(n_sweeps), _stream(stream)), "rsos_sweep")
+
+
+def rsos_width(h, surfaces: int, stream=None, allow_overflow: bool = False):
+    """Measure now.  Returns (sum_h, sum_h2, w2, t) with int64/float64 arrays of
+    length ``surfaces``."""
+    s1 = np.zeros(surfaces, dtype=np.int64)
+    s2 = np.zeros(surfaces, dtype=np.int64)
+    w2 = np.zeros(surfaces, dtype=np.float64)
+    t = ctypes.c_int64()
+    _check(_load().rsos_width(h, _p(s1, ctypes.c_int64), _p(s2, ctypes.c_int64), _p(w2, ctypes.c_double),
+                              ctypes.byref(t), _stream(stream)),
+           "rsos_width", allow=(RSOS_EOVERFLOW,) if allow_overflow else ())
+    return s1, s2, w2, t.value
+
+
+def rsos_schedule(h, times) -> None:
+    a = np.ascontiguousarray(times, dtype=np.int64)
+    _check(_load().rsos_schedule(h, _p(a, ctypes.c_int64), len(a)), "rsos_schedule")
+
+
+def rsos_read_series(h, surfaces: int, cap: int, stream=None, allow_overflow: bool = False):
+    """Returns (times[n], sum_h[n, S], sum_h2[n, S], w2[n, S])."""
+    times = np.zeros(cap, dtype=np.int64)
+    s1 = np.zeros((cap, surfaces), dtype=np.int64)
+    s2 = np.zeros((cap, surfaces), dtype=np.int64)
+    w2 = np.zeros((cap, surfaces), dtype=np.float64)
+    n = ctypes.c_int32()
+    _check(_load().rsos_read_series(h, _p(times, ctypes.c_int64), _p(s1, ctypes.c_int64), _p(s2, ctypes.c_int64),
+                                    _p(w2, ctypes.c_double), int(cap), ctypes.byref(n), _stream(stream)),
+           "rsos_read_series", allow=(RSOS_EOVERFLOW,) if allow_overflow else ())
+    k = n.value
+    return times[:k], s1[:k], s2[:k], w2[:k]
+
+
+def rsos_heights(h, surface: int, L: int, stream=None) -> np.ndarray:
+    out = np.zeros((L, L), dtype=np.int64)
+    _check(_load().rsos_heights(h, int(surface), _p(out, ctypes.c_int64), _stream(stream)), "rsos_heights")
+    return out
+
+
+def rsos_time(h) -> int:
+    t = ctypes.c_int64()
+    _check(_load().rsos_time(h, ctypes.byref(t)), "rsos_time")
+    return t.value
+
+
+def rsos_free(h) -> None:
+    _check(_load().rsos_free(h), "rsos_free")
+
+
+def rsos_last_cuda_error(h) -> int:
+    return int(_load().rsos_last_cuda_error(h))
+
+
+def rsos_batch_create(params_list, t_max, hbm_budget: int = 0):
+    n = len(params_list)
+    arr = (rsos_params * n)(*params_list)
+    tm = np.ascontiguousarray(t_max, dtype=np.int64)
+    b = ctypes.c_void_p()
+    _check(_load().rsos_batch_create(arr, _p(tm, ctypes.c_int64), n, int(hbm_budget), ctypes.byref(b)),
+           "rsos_batch_create")
+    return b
+
+
+def rsos_batch_schedule(b, job: int, times) -> None:
+    a = np.ascontiguousarray(times, dtype=np.int64)
+    _check(_load().rsos_batch_schedule(b, int(job), _p(a, ctypes.c_int64), len(a)), "rsos_batch_schedule")
+
+
+def rsos_batch_run(b, stream=None) -> None:
+    _check(_load().rsos_batch_run(b, _stream(stream)), "rsos_batch_run")
+
+
+def rsos_batch_poll(b, cap: int = 4096):
+    """Returns (status, finished job ids); status is RSOS_OK or RSOS_EBUSY."""
+    ids = np.zeros(max(cap, 1), dtype=np.int32)
+    n = ctypes.c_int32()
+    rc = _check(_load().rsos_batch_poll(b, _p(ids, ctypes.c_int32), int(cap), ctypes.byref(n)),
+                "rsos_batch_poll", allow=(RSOS_EBUSY,))
+    return rc, [int(v) for v in ids[:n.value]]
+
+
+def rsos_batch_job(b, job: int):
+    h = ctypes.c_void_p()
+    _check(_load().rsos_batch_job(b, int(job), ctypes.byref(h)), "rsos_batch_job")
+    return h
+
+
+def rsos_batch_free(b) -> None:
+    _check(_load().rsos_batch_free(b), "rsos_batch_free")

@@ -1,0 +1,42 @@
+// Host-side launch interface between the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "rsos_device.cuh"
+
+namespace rsos {
+
+// Sweep kernels, one translation unit per sub-tile edge SX in {1, 2, 4, 8}.
+// Launch one phase (set q = perm[p] of sweep t) over every tile of the job.
+// words_per_thread: 1 (uint32 lane words) or 2 (uint64); smem_budget: bytes of
+// dynamic shared memory a block may use.
+cudaError_t launch_phase(const JobDev& J, int SX, int words_per_thread, uint32_t t, int p, int q,
+                         int ox, int oy, const Origin00& o, size_t smem_budget, cudaStream_t s);
+cudaError_t launch_phase_plain(const JobDev& J, int SX, uint32_t t, int p, int q, int ox, int oy,
+                               size_t smem_budget, cudaStream_t s);
+
+#define RSOS_DECLARE_SX(SX)                                                                          \
+    cudaError_t launch_phase_s##SX(const JobDev& J, int words_per_thread, uint32_t t, int p, int q,  \
+                                   int ox, int oy, const Origin00& o, size_t smem_budget,           \
+                                   cudaStream_t s);                                                  \
+    cudaError_t launch_phase_plain_s##SX(const JobDev& J, uint32_t t, int p, int q, int ox, int oy,  \
+                                         size_t smem_budget, cudaStream_t s);
+RSOS_DECLARE_SX(1)
+RSOS_DECLARE_SX(2)
+RSOS_DECLARE_SX(4)
+RSOS_DECLARE_SX(8)
+#undef RSOS_DECLARE_SX
+
+// Measurement (Eq. 2 numerators), exact: fills rec[S_pad][4] with the 128-bit
+// sum h and sum h^2 of every lane as (lo, hi) int64 pairs.
+cudaError_t launch_measure(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial,
+                           int ncb_capacity, int64_t* rec, cudaStream_t s);
+// Number of column blocks the measurement needs (partial buffer rows).
+int measure_blocks(const JobDev& J, bool plain);
+// Absolute heights of one lane into out[L*L] (int64).
+cudaError_t launch_heights(const JobDev& J, bool plain, int lane, int32_t* row0, int64_t* out,
+                           cudaStream_t s);
+// Zero-fill (flat initial condition).
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+
+}  // namespace rsos

@@ -1,0 +1,268 @@
+// Exact width measurement (Eq. 2) of multisurface-coded lattices, plus the
+// flat-start initialisation (section II).
+//
+// The coded lattice holds h mod 2^B per site and lane.  Neighbour
+// differences decode uniquely because |h(x) - h(n)| <= N < 2^(B-1): the B-bit
+// residue of h(n) - h(x) read as a two's-complement number IS the difference.
+// Heights relative to site (0,0) follow by summing differences along row 0
+// and then down every column; with the tracked absolute height h00 of site
+// (0,0) per lane,
+//     sum h   = L^2 h00 + sum rel
+//     sum h^2 = L^2 h00^2 + 2 h00 sum rel + sum rel^2
+// in 128-bit integers.  Kernels:
+//   row0_prefix_kernel   rel(x, 0) for every lane (one block per lane word)
+//   column_walk_kernel   per column and lane, sum rel and sum rel^2 down y
+//   finalize_kernel      per lane, 128-bit totals combined with h00
+#include "rsos_launch.h"
+
+namespace rsos {
+
+__device__ __forceinline__ size_t site_word(const JobDev& J, int x, int y, int w)
+{
+    return (((size_t)y * J.T + (size_t)(x % J.T)) * J.nT + (size_t)(x / J.T)) * J.NW + w;
+}
+
+__device__ __forceinline__ int lane_residue(const JobDev& J, int x, int y, int w, int lane)
+{
+    const size_t idx = site_word(J, x, y, w);
+    const size_t plane = (size_t)J.L * J.L * J.NW;
+    int v = 0;
+    for (int b = 0; b < J.B; ++b) v |= (int)((J.planes[b * plane + idx] >> lane) & 1u) << b;
+    return v;
+}
+
+// h(b) - h(a) from the residues a, b (B-bit two's complement).
+__device__ __forceinline__ int residue_diff(int a, int b, int B)
+{
+    const int d = (b - a) & ((1 << B) - 1);
+    return d >= (1 << (B - 1)) ? d - (1 << B) : d;
+}
+
+__global__ void __launch_bounds__(1024) row0_prefix_kernel(JobDev J, int32_t* __restrict__ row0)
+{
+    __shared__ int32_t chunk_sum[32][33];
+    const int w = blockIdx.x, lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const int L = J.L, B = J.B;
+    const int per = (L + 31) / 32;
+    const int x0 = min(L, c * per), x1 = min(L, x0 + per);
+    int s = 0;
+    if (x0 < x1) {
+        int vprev = lane_residue(J, x0, 0, w, lane);
+        for (int x = x0; x < x1 && x + 1 < L; ++x) {
+            const int v = lane_residue(J, x + 1, 0, w, lane);
+            s += residue_diff(vprev, v, B);
+            vprev = v;
+        }
+    }
+    chunk_sum[c][lane] = s;
+    __syncthreads();
+    int rel = 0;
+    for (int cc = 0; cc < c; ++cc) rel += chunk_sum[cc][lane];
+    if (x0 < x1) {
+        int32_t* out = row0 + (size_t)(w * 32 + lane) * L;
+        int vprev = lane_residue(J, x0, 0, w, lane);
+        for (int x = x0; x < x1; ++x) {
+            out[x] = rel;
+            if (x + 1 < L) {
+                const int v = lane_residue(J, x + 1, 0, w, lane);
+                rel += residue_diff(vprev, v, B);
+                vprev = v;
+            }
+        }
+    }
+}
+
+// grid (T * ceil(nT/32), NW), 128 threads: 32 columns of one class x 4 groups
+// of 8 lanes of word blockIdx.y.
+__global__ void __launch_bounds__(128) column_walk_kernel(JobDev J, const int32_t* __restrict__ row0,
+                                                          int S_pad, int64_t* __restrict__ partial)
+{
+    const int w = blockIdx.y, cb = blockIdx.x;
+    const int T = J.T, nT = J.nT, L = J.L, B = J.B;
+    const int u = cb % T;
+    const int m = (cb / T) * 32 + (threadIdx.x & 31);
+    const int lg = threadIdx.x >> 5;
+    const bool valid = m < nT;
+    const int x = m * T + u;
+    int rel[8], vprev[8];
+    long long s1[8], s2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        rel[j] = 0;
+        vprev[j] = 0;
+        s1[j] = 0;
+        s2[j] = 0;
+    }
+    if (valid) {
+        const size_t plane = (size_t)L * L * J.NW;
+        const size_t row_stride = (size_t)T * nT * J.NW;
+        size_t idx = site_word(J, x, 0, w);
+        uint32_t wv[4];
+        for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int lane = lg * 8 + j;
+            rel[j] = row0[(size_t)(w * 32 + lane) * L + x];
+            int v = 0;
+            for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> j) & 1u) << b;
+            vprev[j] = v;
+            s1[j] = rel[j];
+            s2[j] = (long long)rel[j] * rel[j];
+        }
+        for (int y = 1; y < L; ++y) {
+            idx += row_stride;
+            for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                int v = 0;
+                for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> j) & 1u) << b;
+                rel[j] += residue_diff(vprev[j], v, B);
+                vprev[j] = v;
+                s1[j] += rel[j];
+                s2[j] += (long long)rel[j] * rel[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        long long a = s1[j], b = s2[j];
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, off);
+            b += __shfl_down_sync(0xffffffffu, b, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            const size_t r = ((size_t)cb * S_pad + (size_t)w * 32 + lg * 8 + j) * 2;
+            partial[r] = a;
+            partial[r + 1] = b;
+        }
+    }
+}
+
+// Plain path: absolute heights, one partial row per block (lane 0 only).
+__global__ void __launch_bounds__(256) plain_sum_kernel(const int32_t* __restrict__ h, long long n,
+                                                        int64_t* __restrict__ partial)
+{
+    long long a = 0, b = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long v = h[k];
+        a += v;
+        b += v * v;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    __shared__ long long sa[8], sb[8];
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long ta = 0, tb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            ta += sa[k];
+            tb += sb[k];
+        }
+        partial[(size_t)blockIdx.x * 2] = ta;
+        partial[(size_t)blockIdx.x * 2 + 1] = tb;
+    }
+}
+
+__global__ void finalize_kernel(const int64_t* __restrict__ partial, int nrows, int S_pad, int L,
+                                const int64_t* __restrict__ h00, int64_t* __restrict__ rec)
+{
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lane >= S_pad) return;
+    __int128 s1 = 0, s2 = 0;
+    for (int r = 0; r < nrows; ++r) {
+        s1 += (__int128)partial[((size_t)r * S_pad + lane) * 2];
+        s2 += (__int128)partial[((size_t)r * S_pad + lane) * 2 + 1];
+    }
+    const __int128 h0 = h00 ? (__int128)h00[lane] : (__int128)0;
+    const __int128 area = (__int128)L * L;
+    const __int128 sh = area * h0 + s1;
+    const __int128 sh2 = area * h0 * h0 + 2 * h0 * s1 + s2;
+    rec[(size_t)lane * 4 + 0] = (int64_t)(uint64_t)sh;
+    rec[(size_t)lane * 4 + 1] = (int64_t)(sh >> 64);
+    rec[(size_t)lane * 4 + 2] = (int64_t)(uint64_t)sh2;
+    rec[(size_t)lane * 4 + 3] = (int64_t)(sh2 >> 64);
+}
+
+// Heights of one lane: thread per column, walking down y from row 0.
+__global__ void heights_kernel(JobDev J, int lane, const int32_t* __restrict__ row0, int64_t* __restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= J.L) return;
+    const int w = lane >> 5, bit = lane & 31;
+    const int64_t h0 = J.h00[lane];
+    int rel = row0[(size_t)lane * J.L + x];
+    int vprev = lane_residue(J, x, 0, w, bit);
+    out[x] = h0 + rel;
+    for (int y = 1; y < J.L; ++y) {
+        const int v = lane_residue(J, x, y, w, bit);
+        rel += residue_diff(vprev, v, J.B);
+        vprev = v;
+        out[(size_t)y * J.L + x] = h0 + rel;
+    }
+}
+
+__global__ void plain_heights_kernel(const int32_t* __restrict__ h, long long n, int64_t* __restrict__ out)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        out[k] = h[k];
+}
+
+__global__ void zero_kernel(uint4* __restrict__ p, size_t n16, unsigned char* __restrict__ tail, size_t ntail)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n16; k += stride) p[k] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x == 0 && threadIdx.x < ntail) tail[threadIdx.x] = 0;
+}
+
+int measure_blocks(const JobDev& J, bool plain)
+{
+    if (plain) return 256;
+    return J.T * ((J.nT + 31) / 32);
+}
+
+cudaError_t launch_measure(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial, int ncb_capacity,
+                           int64_t* rec, cudaStream_t s)
+{
+    const int ncb = measure_blocks(J, plain);
+    if (ncb > ncb_capacity) return cudaErrorInvalidValue;
+    if (plain) {
+        plain_sum_kernel<<<ncb, 256, 0, s>>>(J.heights, (long long)J.L * J.L, partial);
+        finalize_kernel<<<1, 32, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec);
+        return cudaGetLastError();
+    }
+    row0_prefix_kernel<<<J.NW, 1024, 0, s>>>(J, row0);
+    column_walk_kernel<<<dim3(ncb, J.NW), 128, 0, s>>>(J, row0, S_pad, partial);
+    finalize_kernel<<<(S_pad + 127) / 128, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heights(const JobDev& J, bool plain, int lane, int32_t* row0, int64_t* out, cudaStream_t s)
+{
+    if (plain) {
+        plain_heights_kernel<<<256, 256, 0, s>>>(J.heights, (long long)J.L * J.L, out);
+        return cudaGetLastError();
+    }
+    row0_prefix_kernel<<<J.NW, 1024, 0, s>>>(J, row0);
+    heights_kernel<<<(J.L + 127) / 128, 128, 0, s>>>(J, lane, row0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s)
+{
+    const size_t n16 = bytes / 16, ntail = bytes % 16;
+    size_t blocks = (n16 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks == 0) blocks = 1;
+    zero_kernel<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<uint4*>(p), n16,
+                                                  reinterpret_cast<unsigned char*>(p) + n16 * 16, ntail);
+    return cudaGetLastError();
+}
+
+}  // namespace rsos

@@ -1,0 +1,74 @@
+// Host build of the CUDA path's header-only logic (philox.cuh, rsos_logic.cuh,
+// locate_origin_site) for CPU tests.  Compiled by tests/test_logic_host.py.
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "rsos_device.cuh"
+#include "rsos_logic.cuh"
+
+// One word step: residues of x and its four neighbours for 64 lanes (one
+// residue per lane, values < 2^B), lane mask m; returns the accept mask and
+// the new residues of x.
+template <int N>
+static uint64_t step_n(const int* xr, const int* er, const int* wr, const int* nr, const int* sr, uint64_t m,
+                       int* xout)
+{
+    constexpr int B = rsos::bits_for_step(N);
+    uint64_t x[B] = {}, e[B] = {}, w[B] = {}, n[B] = {}, s[B] = {};
+    for (int j = 0; j < 64; ++j)
+        for (int b = 0; b < B; ++b) {
+            x[b] |= (uint64_t)((xr[j] >> b) & 1) << j;
+            e[b] |= (uint64_t)((er[j] >> b) & 1) << j;
+            w[b] |= (uint64_t)((wr[j] >> b) & 1) << j;
+            n[b] |= (uint64_t)((nr[j] >> b) & 1) << j;
+            s[b] |= (uint64_t)((sr[j] >> b) & 1) << j;
+        }
+    const uint64_t acc = rsos::accept_mask<N, B, uint64_t>(m, x, e, w, n, s);
+    rsos::masked_increment<B, uint64_t>(x, acc);
+    for (int j = 0; j < 64; ++j) {
+        int v = 0;
+        for (int b = 0; b < B; ++b) v |= (int)((x[b] >> j) & 1) << b;
+        xout[j] = v;
+    }
+    return acc;
+}
+
+
+extern "C" {
+
+void probe_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out)
+{
+    const rsos::U4 r = rsos::philox4x32_10(rsos::U4{ctr[0], ctr[1], ctr[2], ctr[3]}, key[0], key[1]);
+    out[0] = r.x; out[1] = r.y; out[2] = r.z; out[3] = r.w;
+}
+
+void probe_control(uint64_t seed, uint32_t t, int T, int order, int* out6)
+{
+    const rsos::Control c = rsos::sweep_control((uint32_t)seed, (uint32_t)(seed >> 32), t, T, T, order);
+    out6[0] = c.ox; out6[1] = c.oy;
+    for (int m = 0; m < 4; ++m) out6[2 + m] = c.perm[m];
+}
+
+void probe_origin(int L, int T, int ox, int oy, int* out4)
+{
+    const rsos::Origin00 o = rsos::locate_origin_site(L, T, ox, oy);
+    out4[0] = o.tx; out4[1] = o.ty; out4[2] = o.q; out4[3] = o.k;
+}
+
+uint64_t probe_step(int N, const int* xr, const int* er, const int* wr, const int* nr, const int* sr, uint64_t m,
+                    int* xout)
+{
+    switch (N) {
+        case 1: return step_n<1>(xr, er, wr, nr, sr, m, xout);
+        case 2: return step_n<2>(xr, er, wr, nr, sr, m, xout);
+        case 3: return step_n<3>(xr, er, wr, nr, sr, m, xout);
+        case 4: return step_n<4>(xr, er, wr, nr, sr, m, xout);
+        case 5: return step_n<5>(xr, er, wr, nr, sr, m, xout);
+        case 6: return step_n<6>(xr, er, wr, nr, sr, m, xout);
+        case 7: return step_n<7>(xr, er, wr, nr, sr, m, xout);
+        default: return 0;
+    }
+}
+
+int probe_bits(int N) { return rsos::bits_for_step(N); }
+}

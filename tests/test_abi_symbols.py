@@ -1,0 +1,45 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/rsos.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(rsos_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1605_02620_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert {"rsos_init", "rsos_sweep", "rsos_width", "rsos_free"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_header():
+    import paper_1605_02620_gb300 as R
+    for n in _declared():
+        assert hasattr(R, n), n
+    assert R.rsos_strerror(-1) == "invalid argument"
+
+
+def test_invalid_params_rejected_without_gpu():
+    import paper_1605_02620_gb300 as R
+    import pytest
+    for bad in [R.rsos_params(L=12, N=1, surfaces=64), R.rsos_params(L=64, N=0, surfaces=1),
+                R.rsos_params(L=64, N=8, surfaces=1), R.rsos_params(L=64, N=1, surfaces=0),
+                R.rsos_params(L=64, N=1, surfaces=1, tile=6)]:
+        with pytest.raises(R.RsosError):
+            R.rsos_required_bytes(bad)
+    assert R.rsos_required_bytes(R.rsos_params(L=4096, N=1, surfaces=64)) >= 2 * 4096 * 4096 * 8

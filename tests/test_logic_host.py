@@ -1,0 +1,106 @@
+"""CPU checks of the CUDA path's header-only logic, compiled for the host.
+
+* the bit-sliced accept test and masked increment equal Eq. 6 applied lane by
+  lane, exhaustively over every legal neighbourhood for N = 1..7;
+* the device Philox and per-sweep control draw agree with the oracle's
+  independent implementation (the two share no code);
+* the location of site (0,0) in a shifted tiling.
+"""
+import ctypes
+import itertools
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1605_02620_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("probe") / "logic_probe.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC,
+                           os.path.join(HERE, "host", "logic_probe.cpp"), "-o", out])
+    lib = ctypes.CDLL(out)
+    ip = ctypes.POINTER(ctypes.c_int)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.probe_philox.argtypes = [u32p, u32p, u32p]
+    lib.probe_control.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ip]
+    lib.probe_origin.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
+    lib.probe_step.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip, ctypes.c_uint64, ip]
+    lib.probe_step.restype = ctypes.c_uint64
+    lib.probe_bits.restype = ctypes.c_int
+    return lib
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_word_logic_exhaustive(probe, N):
+    B = probe.probe_bits(N)
+    assert 2 ** B >= 2 * N + 1 and 2 ** (B - 1) < 2 * N + 1
+    M = 2 ** B
+    rng = np.random.Generator(np.random.PCG64(N))
+    # every (h_x mod 2^B, d_E, d_W, d_N, d_S) with d in [-N, N]
+    cases = np.array([(hx,) + d for hx in range(M)
+                      for d in itertools.product(range(-N, N + 1), repeat=4)], dtype=np.int64)
+    pad = (-len(cases)) % 64
+    cases = np.concatenate([cases, cases[:pad]])
+    for chunk in cases.reshape(-1, 64, 5):
+        hx = chunk[:, 0]
+        nb = [(hx + chunk[:, 1 + k]) % M for k in range(4)]
+        for m in (0xFFFFFFFFFFFFFFFF, int(rng.integers(0, 2 ** 63)) * 2 + 1):
+            xin = np.ascontiguousarray(hx, dtype=np.int32)
+            args = [np.ascontiguousarray(v, dtype=np.int32) for v in nb]
+            xout = np.zeros(64, dtype=np.int32)
+            acc = probe.probe_step(N, _ip(xin), *[_ip(a) for a in args], m, _ip(xout))
+            for j in range(64):
+                # Eq. 6: after the deposit every |h(x)+1 - h(n)| <= N
+                ok = all(abs(1 - chunk[j, 1 + k]) <= N for k in range(4))
+                want = bool((m >> j) & 1) and ok
+                assert bool((acc >> j) & 1) == want
+                assert xout[j] == ((hx[j] + 1) % M if want else hx[j])
+
+
+def test_device_philox_matches_oracle(probe):
+    rng = np.random.Generator(np.random.PCG64(5))
+    for _ in range(2000):
+        ctr = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+        out = np.zeros(4, dtype=np.uint32)
+        u32 = ctypes.POINTER(ctypes.c_uint32)
+        probe.probe_philox(ctr.ctypes.data_as(u32), key.ctypes.data_as(u32), out.ctypes.data_as(u32))
+        assert np.array_equal(out, O.philox4x32_10(ctr, key))
+
+
+@pytest.mark.parametrize("T,order", [(8, 0), (2, 0), (16, 1), (4, 0)])
+def test_device_control_matches_oracle(probe, T, order):
+    seed = 0xABCDEF0123456789
+    p = O.Params(L=64, N=1, Tx=T, Ty=T, phase_order=order, seed=seed)
+    out = np.zeros(6, dtype=np.int32)
+    for t in range(0, 5000, 7):
+        probe.probe_control(seed, t, T, order, _ip(out))
+        ox, oy, perm = O.control(p, t)
+        assert (out[0], out[1], tuple(out[2:])) == (ox, oy, perm)
+
+
+def test_origin_site_location(probe):
+    out = np.zeros(4, dtype=np.int32)
+    for L, T in [(64, 8), (16, 4), (2, 2), (48, 16)]:
+        S = T // 2
+        for ox in range(T):
+            for oy in range(T):
+                probe.probe_origin(L, T, ox, oy, _ip(out))
+                tx, ty, q, k = out
+                # reconstruct the absolute coordinates of that sub-tile site
+                qx, qy = q & 1, q >> 1
+                x = (ox + tx * T + qx * S + k % S) % L
+                y = (oy + ty * T + qy * S + k // S) % L
+                assert (x, y) == (0, 0)
