@@ -33,9 +33,10 @@ METRIC = "RSOS site-update attempts/s on 1 GB300 (plain vs batched); % HBM roofl
 WORKLOAD = dict(workload="ms-n1: L=4096 periodic, N=1, 64 surfaces bit-sliced in uint64 words, 8x8 DT tiles, "
                          "flat start, 1e4 sweeps, W^2 per surface at 40 log-spaced times",
                 L=4096, N=1, surfaces=64, tile=8, sweeps=10000, measurements=40)
-KERNEL_SOURCES = ["paper_1605_02620_gb300/csrc/rsos_device.cuh", "paper_1605_02620_gb300/csrc/rsos_sweep.cuh",
-                  "paper_1605_02620_gb300/csrc/rsos_logic.cuh", "paper_1605_02620_gb300/csrc/philox.cuh"]
-PROFILE = os.path.join(ROOT, "profiles", "phase_kernel_L4096_N1_S64.md")
+KERNEL_SOURCES = ["paper_1605_02620_gb300/csrc/rsos_device.cuh", "paper_1605_02620_gb300/csrc/rsos_persist.cuh",
+                  "paper_1605_02620_gb300/csrc/rsos_sched.cuh", "paper_1605_02620_gb300/csrc/rsos_logic.cuh",
+                  "paper_1605_02620_gb300/csrc/philox.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "persistent_kernel_L4096_N1_S64.md")
 
 
 def kernel_hash() -> str:
@@ -157,11 +158,14 @@ def run_gpu(args):
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     base = (buf.data_ptr() + 255) // 256 * 256
 
+    launches = [0]
+
     def one_job(device_timed=True):
         h = R.rsos_init(params, dev_buf=base, dev_bytes=nbytes, stream=stream)
         R.rsos_schedule(h, times)
         R.rsos_sweep(h, sweeps, stream=stream)
         ts, s1, s2, w2 = R.rsos_read_series(h, S, len(times) + 1, stream=stream)
+        launches[0] = R.rsos_launches(h)
         R.rsos_free(h)
         return ts, w2
 
@@ -182,8 +186,13 @@ def run_gpu(args):
     clk = clocks.stop()
     dev_ms = ev0.elapsed_time(ev1)
     dev_ms = dist_max(dev_ms, world)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": dev_ms / args.steps, "sweeps": sweeps}), flush=True)
+        return
 
-    # Dominant kernel (the phase kernel), timed alone on the same stream.
+    # Dominant kernel, timed alone on the same stream: one persistent launch
+    # of n_kernel_sweeps sweeps (no measurement inside).
     h = R.rsos_init(params, dev_buf=base, dev_bytes=nbytes, stream=stream)
     R.rsos_sweep(h, 50, stream=stream)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -193,7 +202,7 @@ def run_gpu(args):
     k1.record(stream)
     torch.cuda.synchronize()
     R.rsos_free(h)
-    launch_ms = k0.elapsed_time(k1) / (4 * n_kernel_sweeps)
+    launch_ms = k0.elapsed_time(k1)
 
     # End to end through the public API with host buffers: the library
     # allocates device memory, runs, and the series is copied to host arrays.
@@ -215,9 +224,9 @@ def run_gpu(args):
     value = attempts * world * args.steps / (dev_ms / 1e3)
     e2e_value = attempts * world * e2e_steps / e2e_s
     peaks, peak_src = measured_peaks()
-    alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S / 4.0  # per phase launch
+    alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S * n_kernel_sweeps  # per launch
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    launches_per_job = 1 + 4 * sweeps + 3 * len(times)
+    launches_per_job = launches[0]
     if rank != 0:
         return
     cpu = cpu_baseline(L, W["N"], W["tile"], seed) if world == 1 else None
@@ -231,7 +240,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": (len(times)) * S * 4 * 8 + 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
-                     "kernel": "rsos::phase_kernel<1, uint64_t, 4>", "launch_ms": launch_ms,
+                     "kernel": "rsos::persistent_kernel<1, uint64_t, 4>", "launch_ms": launch_ms,
+                     "sweeps_per_launch": n_kernel_sweeps,
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -302,7 +312,18 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"],
+                    help="sweeps per job (reduced values only for profiling captures)")
+    ap.add_argument("--measurements", type=int, default=WORKLOAD["measurements"],
+                    help="measurement times per job (reduced values only for profiling captures)")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling capture: timed steps only (no kernel timing, e2e or CPU baseline)")
     args = ap.parse_args()
+    if args.sweeps != WORKLOAD["sweeps"] or args.measurements != WORKLOAD["measurements"]:
+        WORKLOAD["sweeps"] = args.sweeps
+        WORKLOAD["measurements"] = max(2, min(args.measurements, args.sweeps))
+        WORKLOAD["workload"] += (f" [reduced to {args.sweeps} sweeps, {WORKLOAD['measurements']} measurements"
+                                 " for profiling]")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -127,6 +127,19 @@ int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* su
  * (row-major, x fastest, int64 [L*L]).  Synchronises the stream. */
 int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream);
 
+/* Fault-detection self-test of the persistent engine (no counterpart in the
+ * paper).  Queues one launch whose every dependency wait can never be
+ * satisfied (it asks for sweep t+2 before t+1 ran), so each wait expires after
+ * budget_ns nanoseconds; checks that the launch reported the expiry, clears
+ * the error word and returns RSOS_ETIMEOUT.  The lattice and t are untouched
+ * and the handle stays usable.  RSOS_EINVAL unless the handle uses the
+ * persistent engine.  Synchronises the stream. */
+int rsos_selftest_timeout(rsos_handle* h, int64_t budget_ns, void* stream);
+
+/* Number of CUDA kernels this handle has queued so far (initialisation,
+ * sweeps, measurements); for accounting and benchmarks. */
+int rsos_launches(const rsos_handle* h, int64_t* out);
+
 /* Current time of the handle (completed sweeps). */
 int rsos_time(const rsos_handle* h, int64_t* t_out);
 
@@ -137,7 +150,8 @@ int rsos_free(rsos_handle* h);
 /* Static description of a status code. */
 const char* rsos_strerror(int status);
 
-/* CUDA error code behind the last RSOS_ECUDA of the handle (0 if none). */
+/* CUDA error code behind the last RSOS_ECUDA of the handle (0 if none); with
+ * h == NULL, the CUDA error of the last failed rsos_init on this thread. */
 int rsos_last_cuda_error(const rsos_handle* h);
 
 /* ---------------------------------------------------------------------------

@@ -21,6 +21,7 @@ import numpy as np
 __all__ = [
     "RsosError", "rsos_params", "rsos_required_bytes", "rsos_init", "rsos_sweep", "rsos_width",
     "rsos_schedule", "rsos_read_series", "rsos_heights", "rsos_time", "rsos_free", "rsos_strerror",
+    "rsos_selftest_timeout", "rsos_launches",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "library_path",
 ]
@@ -41,9 +42,11 @@ _lib = None
 
 
 class RsosError(RuntimeError):
-    def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {rsos_strerror(status)} ({status})")
+    def __init__(self, status: int, what: str, cuda_error: int = 0):
+        extra = f", cuda error {cuda_error}" if cuda_error else ""
+        super().__init__(f"{what}: {rsos_strerror(status)} ({status}{extra})")
         self.status = status
+        self.cuda_error = cuda_error
 
 
 class rsos_params(ctypes.Structure):
@@ -81,6 +84,8 @@ def _load():
             "rsos_read_series": [vp, P(i64), P(i64), P(i64), P(ctypes.c_double), i32, P(i32), vp],
             "rsos_heights": [vp, i32, P(i64), vp],
             "rsos_time": [vp, P(i64)],
+            "rsos_selftest_timeout": [vp, i64, vp],
+            "rsos_launches": [vp, P(i64)],
             "rsos_free": [vp],
             "rsos_last_cuda_error": [vp],
             "rsos_batch_create": [P(rsos_params), P(i64), i32, sz, P(vp)],
@@ -141,8 +146,9 @@ def rsos_init(params: rsos_params, dev_buf=None, dev_bytes: int = 0, stream=None
             if not dev_bytes:
                 dev_bytes = int(dev_buf.numel() * dev_buf.element_size())
     h = ctypes.c_void_p()
-    _check(_load().rsos_init(ctypes.byref(params), ptr, int(dev_bytes), _stream(stream), ctypes.byref(h)),
-           "rsos_init")
+    rc = _load().rsos_init(ctypes.byref(params), ptr, int(dev_bytes), _stream(stream), ctypes.byref(h))
+    if rc != RSOS_OK:
+        raise RsosError(rc, "rsos_init", _load().rsos_last_cuda_error(None) if rc == RSOS_ECUDA else 0)
     return h
 
 
@@ -186,6 +192,19 @@ def rsos_heights(h, surface: int, L: int, stream=None) -> np.ndarray:
     out = np.zeros((L, L), dtype=np.int64)
     _check(_load().rsos_heights(h, int(surface), _p(out, ctypes.c_int64), _stream(stream)), "rsos_heights")
     return out
+
+
+def rsos_selftest_timeout(h, budget_ns: int, stream=None) -> int:
+    """Force every dependency wait of one persistent launch to expire; returns
+    the status (RSOS_ETIMEOUT when the device reported the expiry)."""
+    return _check(_load().rsos_selftest_timeout(h, int(budget_ns), _stream(stream)), "rsos_selftest_timeout",
+                  allow=(RSOS_ETIMEOUT,))
+
+
+def rsos_launches(h) -> int:
+    n = ctypes.c_int64()
+    _check(_load().rsos_launches(h, ctypes.byref(n)), "rsos_launches")
+    return n.value
 
 
 def rsos_time(h) -> int:

@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             futs = [ex.submit(_compile, nvcc, s, o, list(extra_flags)) for s, o in jobs]
             for f in futs:
                 f.result()
-    if jobs or not os.path.exists(LIB):
+    if jobs or not os.path.exists(LIB) or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)

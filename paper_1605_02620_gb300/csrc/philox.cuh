@@ -17,16 +17,12 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // golden-ratio Weyl increment
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;  // sqrt(3)-1 Weyl increment
 
+// One 32x32->64 multiply gives both halves.
 RSOS_HD void mul_hi_lo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo)
 {
-#if defined(__CUDA_ARCH__)
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
     const uint64_t p = (uint64_t)a * (uint64_t)b;
     lo = (uint32_t)p;
     hi = (uint32_t)(p >> 32);
-#endif
 }
 
 RSOS_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
@@ -42,6 +38,40 @@ RSOS_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
         c = n;
         k0 += kPhiloxW0;
         k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+// Round keys of one Philox key: k[2r], k[2r+1] are the key words used in
+// round r.  Precomputed once per job so a block evaluates the generator with
+// the keys as uniform kernel-parameter operands.
+struct RoundKeys {
+    uint32_t k[20];
+};
+
+RSOS_HD RoundKeys philox_round_keys(uint32_t k0, uint32_t k1)
+{
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0;
+        rk.k[2 * r + 1] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+RSOS_HD U4 philox4x32_10(U4 c, const RoundKeys& rk)
+{
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_hi_lo(kPhiloxM0, c.x, hi0, lo0);
+        mul_hi_lo(kPhiloxM1, c.z, hi1, lo1);
+        const U4 n = {hi1 ^ c.y ^ rk.k[2 * r], lo1, hi0 ^ c.w ^ rk.k[2 * r + 1], lo0};
+        c = n;
     }
     return c;
 }

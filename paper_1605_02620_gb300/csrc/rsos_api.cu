@@ -38,19 +38,62 @@ struct rsos_handle {
     int sticky;
     int cuda_err;
     size_t smem_budget;
+    // persistent engine
+    bool persist;
+    rsos::PersistPlan plan;
+    uint32_t* table;
+    unsigned long long* done;
+    unsigned long long* ticket;
+    unsigned int* err;
+    long long budget_ns;
+    int64_t launches;  // kernels queued by this handle
 };
 
 namespace {
 
 constexpr int64_t kMaxSweeps = 0xFFFFFFFFll;
 
+// CUDA error of the last failed rsos_init on this thread (no handle exists).
+thread_local int g_init_cuda_err = 0;
+
 struct Layout {
-    size_t planes, h00, row0, partial, rec, total;
+    size_t planes, h00, row0, partial, rec, persist, total;
     int ncb, S_pad, B, NW, T, cap;
-    bool plain;
+    int CW, K;  // persistent engine: tiles per block, chunks per tile row
+    bool plain, persist_on;
 };
 
+// Tiles per lane and work item of the persistent engine (execution geometry
+// only; RSOS_TILES_PER_LANE overrides the default of 2, the fastest measured
+// for L = 4096, N = 1, 64 surfaces on GB300).
+int persist_tiles_per_lane()
+{
+    if (const char* env = std::getenv("RSOS_TILES_PER_LANE")) {
+        const int v = std::atoi(env);
+        if (v >= 1 && v <= 64) return v;
+    }
+    return 2;
+}
+
+// Tiles per work item: one warp's 32 lanes over the lane-word groups of a
+// tile, times the tiles per lane.
+int persist_block_tiles(int NWP)
+{
+    const int cw = 32 / NWP;
+    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane();
+}
+
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// 32-lane words per thread: 2 when the job has an even number of words
+// (uint64 registers), else 1.  RSOS_WORDS_PER_THREAD=1 forces one word per
+// thread (execution geometry only; results are identical).
+int words_per_thread(int NW)
+{
+    if (const char* env = std::getenv("RSOS_WORDS_PER_THREAD"))
+        if (std::atoi(env) == 1) return 1;
+    return (NW % 2 == 0) ? 2 : 1;
+}
 
 int validate(const rsos_params* p)
 {
@@ -64,7 +107,12 @@ int validate(const rsos_params* p)
     if (p->surfaces < 1 || p->surfaces > (1 << 20)) return RSOS_EINVAL;
     if (p->phase_order != 0 && p->phase_order != 1) return RSOS_EINVAL;
     if (p->series_capacity < 0 || p->series_capacity > (1 << 24)) return RSOS_EINVAL;
-    if (p->engine < 0 || p->engine > 1) return RSOS_EINVAL;
+    if (p->engine < 0 || p->engine > 2) return RSOS_EINVAL;
+    if (p->engine == 2 && p->surfaces == 1) return RSOS_EINVAL;  // plain path: phase engine only
+    if (p->engine == 2) {
+        const int NW = (p->surfaces + 31) / 32, NWT = words_per_thread(NW);
+        if (NW / NWT > 32) return RSOS_EINVAL;
+    }
     return RSOS_OK;
 }
 
@@ -89,7 +137,26 @@ Layout layout_of(const rsos_params* p)
     l.row0 = l.plain ? 0 : align256((size_t)l.S_pad * L * 4);
     l.partial = align256((size_t)l.ncb * l.S_pad * 2 * 8);
     l.rec = align256((size_t)(l.cap + 1) * l.S_pad * 4 * 8);
-    l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec;
+    const int nT = p->L / l.T;
+    // Auto engine: the persistent dataflow engine for multisurface jobs with
+    // at least 8 tile rows, one launch per phase otherwise.
+    l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && nT >= 8));
+    if (l.persist_on && p->engine == 0) {
+        // more lane-word groups than lanes of a warp: phase engine
+        const int NWT = words_per_thread(l.NW);
+        if (l.NW / NWT > 32) l.persist_on = false;
+    }
+    l.CW = l.K = 0;
+    l.persist = 0;
+    if (l.persist_on) {
+        const int NWT = words_per_thread(l.NW);
+        const int SX = l.T / 2;
+        (void)SX;
+        l.CW = persist_block_tiles(l.NW / NWT);
+        l.K = (nT + l.CW - 1) / l.CW;
+        l.persist = align256((size_t)4 * nT * 8) + align256((size_t)4 * nT * l.K * 4) + 256;
+    }
+    l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec + l.persist;
     return l;
 }
 
@@ -124,6 +191,7 @@ double width2_from_sums(__int128 sh, __int128 sh2, int64_t L)
 
 int measure_into(rsos_handle* h, int row, cudaStream_t s)
 {
+    h->launches += h->plain ? 2 : 3;
     return fail_cuda(h, rsos::launch_measure(h->J, h->plain, h->S_pad, h->row0, h->partial, h->ncb,
                                              h->rec + (size_t)row * h->S_pad * 4, s));
 }
@@ -154,8 +222,66 @@ int run_sweep(rsos_handle* h, cudaStream_t s)
                             : rsos::launch_phase(h->J, h->SX, h->NWT, t, p, c.perm[p], c.ox, c.oy, o,
                                                  h->smem_budget, s);
         if (e != cudaSuccess) return fail_cuda(h, e);
+        h->launches += 1;
     }
     h->t += 1;
+    return RSOS_OK;
+}
+
+rsos::PersistArgs persist_args(const rsos_handle* h, uint32_t t0, int64_t n)
+{
+    rsos::PersistArgs A;
+    A.J = h->J;
+    A.G.L = h->J.L;
+    A.G.T = h->J.T;
+    A.G.nT = h->J.nT;
+    A.G.K = h->plan.K;
+    A.G.D = h->plan.D;
+    A.G.phase_order = h->p.phase_order;
+    A.G.seed_lo = h->J.seed_lo;
+    A.G.seed_hi = h->J.seed_hi;
+    A.table = h->table;
+    A.done = h->done;
+    A.ticket = h->ticket;
+    A.err = h->err;
+    A.t0 = t0;
+    A.n_tickets = (unsigned long long)n * 4ull * (unsigned long long)h->J.nT * (unsigned long long)h->plan.K;
+    A.CW = h->plan.CW;
+    A.TPL = h->plan.CW / (32 / h->J.NWP);
+    A.budget_ns = h->budget_ns;
+    return A;
+}
+
+int run_persist_segment(rsos_handle* h, int64_t n, cudaStream_t s)
+{
+    // Tickets of one launch stay below 2^31: split very long segments.
+    const int64_t per_sweep = 4ll * h->J.nT * h->plan.K;
+    const int64_t max_sweeps = std::max<int64_t>(1, ((int64_t)1 << 31) / per_sweep);
+    while (n > 0) {
+        const int64_t m = std::min(n, max_sweeps);
+        cudaError_t e = rsos::launch_zero(h->ticket, 8, s);
+        if (e == cudaSuccess)
+            e = rsos::launch_persist(h->J, h->SX, h->NWT, persist_args(h, (uint32_t)h->t, m), h->plan, s);
+        if (e != cudaSuccess) return fail_cuda(h, e);
+        h->launches += 2;
+        h->t += m;
+        n -= m;
+    }
+    return RSOS_OK;
+}
+
+// Reads the persistent engine's error word (synchronises the stream).
+int check_device_error(rsos_handle* h, cudaStream_t s)
+{
+    if (!h->persist) return RSOS_OK;
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->err, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    if (v != 0) {
+        h->sticky = RSOS_ETIMEOUT;
+        return RSOS_ETIMEOUT;
+    }
     return RSOS_OK;
 }
 
@@ -204,6 +330,29 @@ cudaError_t launch_phase_plain(const JobDev& J, int SX, uint32_t t, int p, int q
     }
 }
 
+cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A, const PersistPlan& P,
+                           cudaStream_t s)
+{
+    switch (SX) {
+        case 1: return launch_persist_s1(J, words_per_thread, A, P, s);
+        case 2: return launch_persist_s2(J, words_per_thread, A, P, s);
+        case 4: return launch_persist_s4(J, words_per_thread, A, P, s);
+        case 8: return launch_persist_s8(J, words_per_thread, A, P, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out)
+{
+    switch (SX) {
+        case 1: return plan_persist_s1(J, words_per_thread, block_tiles, out);
+        case 2: return plan_persist_s2(J, words_per_thread, block_tiles, out);
+        case 4: return plan_persist_s4(J, words_per_thread, block_tiles, out);
+        case 8: return plan_persist_s8(J, words_per_thread, block_tiles, out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace rsos
 
 extern "C" {
@@ -233,7 +382,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->SX = l.T / 2;
     h->B = l.B;
     h->NW = l.NW;
-    h->NWT = (l.NW % 2 == 0) ? 2 : 1;
+    h->NWT = words_per_thread(l.NW);
     h->S_pad = l.S_pad;
     h->cap = l.cap;
     h->ncb = l.ncb;
@@ -241,6 +390,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->sched_pos = 0;
     h->sticky = RSOS_OK;
     h->cuda_err = 0;
+    h->launches = l.persist_on ? 3 : 1;
     h->smem_budget = 113 * 1024;
     if (const char* env = std::getenv("RSOS_SMEM_BUDGET")) {
         const long v = std::atol(env);
@@ -274,6 +424,22 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->partial = reinterpret_cast<int64_t*>(cur);
     cur += l.partial;
     h->rec = reinterpret_cast<int64_t*>(cur);
+    cur += l.rec;
+    h->persist = l.persist_on;
+    h->table = nullptr;
+    h->done = nullptr;
+    h->ticket = nullptr;
+    h->err = nullptr;
+    h->budget_ns = 1000000000ll;
+    if (l.persist_on) {
+        const int nT = params->L / l.T;
+        h->done = reinterpret_cast<unsigned long long*>(cur);
+        cur += align256((size_t)4 * nT * 8);
+        h->table = reinterpret_cast<uint32_t*>(cur);
+        cur += align256((size_t)4 * nT * l.K * 4);
+        h->ticket = reinterpret_cast<unsigned long long*>(cur);
+        h->err = reinterpret_cast<unsigned int*>(cur + 8);
+    }
     J.L = params->L;
     J.T = l.T;
     J.nT = params->L / l.T;
@@ -284,9 +450,25 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     J.phase_order = params->phase_order;
     J.seed_lo = (uint32_t)params->seed;
     J.seed_hi = (uint32_t)(params->seed >> 32);
-    // Flat initial condition (section II): planes, h00 and everything else zero.
-    const cudaError_t e = rsos::launch_zero(h->base, l.planes + l.h00, as_stream(stream));
+    J.rk = rsos::philox_round_keys(J.seed_lo, J.seed_hi);
+    cudaError_t e = cudaSuccess;
+    if (l.persist_on) {
+        e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, &h->plan);
+        if (e == cudaSuccess && (h->plan.CW != l.CW || h->plan.K != l.K)) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) {
+            std::vector<uint32_t> table((size_t)4 * J.nT * l.K);
+            rsos::build_order_table(J.nT, l.K, h->plan.D, table.data());
+            e = cudaMemcpyAsync(h->table, table.data(), table.size() * 4, cudaMemcpyHostToDevice, as_stream(stream));
+            if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
+        }
+        if (e == cudaSuccess) e = rsos::launch_zero(h->done, (size_t)4 * J.nT * 8, as_stream(stream));
+        if (e == cudaSuccess) e = rsos::launch_zero(h->ticket, 16, as_stream(stream));
+    }
+    // Flat initial condition (section II): planes and h00 zero.
+    if (e == cudaSuccess) e = rsos::launch_zero(h->base, l.planes + l.h00, as_stream(stream));
     if (e != cudaSuccess) {
+        g_init_cuda_err = (int)e;
+        (void)cudaGetLastError();
         if (h->owns) cudaFree(h->base);
         delete h;
         return RSOS_ECUDA;
@@ -307,8 +489,16 @@ int rsos_sweep(rsos_handle* h, int64_t n_sweeps, void* stream)
     cudaStream_t s = as_stream(stream);
     int rc = measure_due(h, s);
     if (rc) return rc;
-    for (int64_t k = 0; k < n_sweeps; ++k) {
-        rc = run_sweep(h, s);
+    const int64_t t_end = h->t + n_sweeps;
+    while (h->t < t_end) {
+        if (h->persist) {
+            int64_t seg = t_end - h->t;
+            if (h->sched_pos < h->sched.size() && h->sched[h->sched_pos] < t_end)
+                seg = h->sched[h->sched_pos] - h->t;
+            rc = run_persist_segment(h, seg, s);
+        } else {
+            rc = run_sweep(h, s);
+        }
         if (rc) return rc;
         rc = measure_due(h, s);
         if (rc) return rc;
@@ -316,12 +506,40 @@ int rsos_sweep(rsos_handle* h, int64_t n_sweeps, void* stream)
     return RSOS_OK;
 }
 
+int rsos_selftest_timeout(rsos_handle* h, int64_t budget_ns, void* stream)
+{
+    if (!h || budget_ns <= 0) return RSOS_EINVAL;
+    if (!h->persist) return RSOS_EINVAL;
+    if (h->sticky) return h->sticky;
+    cudaStream_t s = as_stream(stream);
+    // Sweep t + 2 depends on sweep t + 1, which never runs: every wait of
+    // this launch expires after budget_ns.
+    const long long saved = h->budget_ns;
+    h->budget_ns = budget_ns;
+    rsos::PersistArgs A = persist_args(h, (uint32_t)(h->t + 2), 1);
+    h->budget_ns = saved;
+    cudaError_t e = rsos::launch_zero(h->ticket, 8, s);
+    if (e == cudaSuccess) e = rsos::launch_persist(h->J, h->SX, h->NWT, A, h->plan, s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    unsigned int v = 0;
+    e = cudaMemcpyAsync(&v, h->err, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    // Clear the error word so the handle stays usable; nothing was written.
+    e = rsos::launch_zero(h->ticket, 16, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    return v != 0 ? RSOS_ETIMEOUT : RSOS_OK;
+}
+
 int rsos_width(rsos_handle* h, int64_t* sum_h, int64_t* sum_h2, double* w2, int64_t* t_out, void* stream)
 {
     if (!h || !sum_h || !sum_h2) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
     cudaStream_t s = as_stream(stream);
-    int rc = measure_into(h, h->cap, s);
+    int rc = check_device_error(h, s);
+    if (rc) return rc;
+    rc = measure_into(h, h->cap, s);
     if (rc) return rc;
     std::vector<int64_t> host((size_t)h->S_pad * 4);
     cudaError_t e = cudaMemcpyAsync(host.data(), h->rec + (size_t)h->cap * h->S_pad * 4, host.size() * 8,
@@ -350,10 +568,12 @@ int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* su
 {
     if (!h || cap < 0 || !n_out) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
+    cudaStream_t s = as_stream(stream);
+    const int rc = check_device_error(h, s);
+    if (rc) return rc;
     const int n = std::min<int>(cap, (int)h->series_t.size());
     *n_out = n;
     if (n == 0) return RSOS_OK;
-    cudaStream_t s = as_stream(stream);
     std::vector<int64_t> host((size_t)n * h->S_pad * 4);
     cudaError_t e = cudaMemcpyAsync(host.data(), h->rec, host.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -373,6 +593,8 @@ int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* strea
     if (!h || !host_LxL || surface < 0 || surface >= h->p.surfaces) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
     cudaStream_t s = as_stream(stream);
+    const int rc = check_device_error(h, s);
+    if (rc) return rc;
     const size_t n = (size_t)h->p.L * h->p.L;
     int64_t* dev = nullptr;
     cudaError_t e = cudaMalloc(&dev, n * 8);
@@ -385,6 +607,13 @@ int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* strea
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dev);
     return fail_cuda(h, e);
+}
+
+int rsos_launches(const rsos_handle* h, int64_t* out)
+{
+    if (!h || !out) return RSOS_EINVAL;
+    *out = h->launches;
+    return RSOS_OK;
 }
 
 int rsos_time(const rsos_handle* h, int64_t* t_out)
@@ -421,6 +650,6 @@ const char* rsos_strerror(int status)
     }
 }
 
-int rsos_last_cuda_error(const rsos_handle* h) { return h ? h->cuda_err : 0; }
+int rsos_last_cuda_error(const rsos_handle* h) { return h ? h->cuda_err : g_init_cuda_err; }
 
 }  // extern "C"

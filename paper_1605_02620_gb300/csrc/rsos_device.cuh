@@ -29,6 +29,7 @@ struct JobDev {
     int32_t N, B;
     int32_t phase_order;
     uint32_t seed_lo, seed_hi;
+    RoundKeys rk;       // Philox round keys of the seed
 };
 
 // Where site (0,0) lies in the tiling of one sweep.
@@ -41,14 +42,21 @@ struct Origin00 {
 RSOS_HD Origin00 locate_origin_site(int L, int T, int ox, int oy)
 {
     const int S = T / 2;
-    const int xr = (L - ox) % L, yr = (L - oy) % L;
+    const int xr = ox == 0 ? 0 : L - ox, yr = oy == 0 ? 0 : L - oy;
     Origin00 o;
     o.tx = xr / T;
     o.ty = yr / T;
-    const int u = xr % T, v = yr % T;
+    const int u = xr - o.tx * T, v = yr - o.ty * T;
     o.q = 2 * (v >= S ? 1 : 0) + (u >= S ? 1 : 0);
-    o.k = (v % S) * S + (u % S);
+    o.k = (v >= S ? v - S : v) * S + (u >= S ? u - S : u);
     return o;
+}
+
+// Same with the tile edge known at compile time (shifts instead of divisions).
+template <int T>
+RSOS_HD Origin00 locate_origin_site_t(int L, int ox, int oy)
+{
+    return locate_origin_site(L, T, ox, oy);
 }
 
 #if defined(__CUDACC__)
@@ -75,14 +83,29 @@ __device__ __forceinline__ uint32_t pick_word(const U4& v, int r)
     return r == 0 ? v.x : r == 1 ? v.y : r == 2 ? v.z : v.w;
 }
 
+// Deposits accepted at site (0,0) raise its tracked absolute height.  Atomic
+// so that blocks of a persistent launch never see a stale cached value.
 template <typename WT>
 __device__ __forceinline__ void record_origin_deposits(int64_t* h00, int lane_base, WT acc)
 {
     while (acc) {
         const int bit = sizeof(WT) == 8 ? __ffsll((long long)acc) - 1 : __ffs((int)acc) - 1;
-        h00[lane_base + bit] += 1;
+        atomicAdd(reinterpret_cast<unsigned long long*>(h00 + lane_base + bit), 1ull);
         acc &= acc - 1;
     }
+}
+
+// Global loads of lattice words.  CG = true bypasses L1 (ld.global.cg): in the
+// persistent engine another block may have rewritten the line since this SM
+// last cached it.
+template <typename WT, bool CG>
+__device__ __forceinline__ WT load_word(const uint32_t* p)
+{
+    if (CG) {
+        if (sizeof(WT) == 8) return (WT)__ldcg(reinterpret_cast<const unsigned long long*>(p));
+        return (WT)__ldcg(reinterpret_cast<const unsigned int*>(p));
+    }
+    return *reinterpret_cast<const WT*>(p);
 }
 
 // Word offsets of the window columns i = -1..SX and rows j = -1..SY of the
@@ -97,7 +120,8 @@ template <int SX>
 __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, int qx, int qy, int ox,
                                              int oy, int w0, WindowIndex<SX>& wi)
 {
-    const int T = J.T, nT = J.nT, L = J.L;
+    constexpr int T = 2 * SX;  // square tiles: the tile edge is known at compile time
+    const int nT = J.nT, L = J.L;
 #pragma unroll
     for (int ii = 0; ii < SX + 2; ++ii) {
         int xr = ox + qx * SX + ii - 1;  // in [-1, 2T)
@@ -127,11 +151,13 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
 //   sm        block shared-memory base, nthr threads, this thread = tid
 //   wp        lane-word group: words wp*NWT .. wp*NWT+NWT-1
 //   t, p, q   sweep index, phase, active sub-tile set q = perm[p]
-template <int N, typename WT, int SX, bool HAS00>
-__device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr,
+template <int N, typename WT, int SX, bool HAS00, bool CG = false, int NTHR = 0>
+__device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
                                                  int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
                                                  int oy, int k00)
 {
+    // A compile-time block size turns every slot offset into an immediate.
+    const int nthr = NTHR > 0 ? NTHR : nthr_rt;
     constexpr int B = bits_for_step(N);
     constexpr int SY = SX;
     constexpr int A = SX * SY;
@@ -155,7 +181,7 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             const int s = jj * WW + ii;
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                const WT v = *reinterpret_cast<const WT*>(J.planes + b * plane + wi.row[jj] + wi.col[ii]);
+                const WT v = load_word<WT, CG>(J.planes + b * plane + wi.row[jj] + wi.col[ii]);
                 sm[(size_t)(s * B + b) * nthr + tid] = v;
             }
         }
@@ -163,43 +189,45 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
 
     const uint32_t tile_id = (uint32_t)(ty * J.nT + tx);
     const uint32_t pbits = (uint32_t)p << 28;
-    U4 site_r = {0u, 0u, 0u, 0u};
+    // Eight selections per site draw (16-bit halves), four per mask draw; the
+    // blocks of eight are unrolled so every word index is static.
 #pragma unroll 1
-    for (int g = 0; g < (NSEL + 3) / 4; ++g) {
-        if ((g & 1) == 0) {
-            site_r = philox4x32_10(U4{tile_id, t, (uint32_t)(g >> 1), kDomSite | pbits}, J.seed_lo, J.seed_hi);
-        }
-        const U4 m_lo = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0},
-                                      J.seed_lo, J.seed_hi);
-        U4 m_hi = m_lo;
-        if (NWT == 2) {
-            m_hi = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)},
-                                 J.seed_lo, J.seed_hi);
-        }
+    for (int g8 = 0; g8 < (NSEL + 7) / 8; ++g8) {
+        const U4 site_r = philox4x32_10(U4{tile_id, t, (uint32_t)g8, kDomSite | pbits}, J.rk);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = 4 * g + r;
-            if (NSEL % 4 != 0 && i >= NSEL) break;
-            const uint32_t word = pick_word(site_r, ((i >> 1) & 3));
-            const uint32_t half = (i & 1) ? (word >> 16) : (word & 0xFFFFu);
-            const uint32_t k = (half * (uint32_t)A) >> 16;
-            const int kx = (int)(k % (uint32_t)SX), ky = (int)(k / (uint32_t)SX);
-            const int s = (ky + 1) * WW + kx + 1;
-            WT* base = sm + (size_t)s * B * nthr + tid;
-            WT x[B], e[B], w[B], n[B], so[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) {
-                x[b] = base[(size_t)b * nthr];
-                e[b] = base[(size_t)(B + b) * nthr];
-                w[b] = base[-(ptrdiff_t)(B - b) * nthr];
-                n[b] = base[-(ptrdiff_t)(WW * B - b) * nthr];
-                so[b] = base[(size_t)(WW * B + b) * nthr];
+        for (int h = 0; h < 2; ++h) {
+            const int g = 2 * g8 + h;
+            if (NSEL % 8 != 0 && 4 * g >= NSEL) break;
+            const U4 m_lo = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0}, J.rk);
+            U4 m_hi = m_lo;
+            if (NWT == 2) {
+                m_hi = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)}, J.rk);
             }
-            const WT acc = accept_mask<N, B, WT>(mask_word<WT>(m_lo, m_hi, r), x, e, w, n, so);
-            masked_increment<B, WT>(x, acc);
 #pragma unroll
-            for (int b = 0; b < B; ++b) base[(size_t)b * nthr] = x[b];
-            if (HAS00 && (int)k == k00) record_origin_deposits<WT>(J.h00, w0 * 32, acc);
+            for (int r = 0; r < 4; ++r) {
+                const int i8 = 4 * h + r;  // selection index within the block of eight
+                if (NSEL % 4 != 0 && 8 * g8 + i8 >= NSEL) break;
+                const uint32_t word = pick_word(site_r, i8 >> 1);
+                const uint32_t half = (i8 & 1) ? (word >> 16) : (word & 0xFFFFu);
+                const uint32_t k = (half * (uint32_t)A) >> 16;
+                const int kx = (int)(k % (uint32_t)SX), ky = (int)(k / (uint32_t)SX);
+                const int s = (ky + 1) * WW + kx + 1;
+                WT* base = sm + (size_t)s * B * nthr + tid;
+                WT x[B], e[B], w[B], n[B], so[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    x[b] = base[(size_t)b * nthr];
+                    e[b] = base[(size_t)(B + b) * nthr];
+                    w[b] = base[-(ptrdiff_t)(B - b) * nthr];
+                    n[b] = base[-(ptrdiff_t)(WW * B - b) * nthr];
+                    so[b] = base[(size_t)(WW * B + b) * nthr];
+                }
+                const WT acc = accept_mask<N, B, WT>(mask_word<WT>(m_lo, m_hi, r), x, e, w, n, so);
+                masked_increment<B, WT>(x, acc);
+#pragma unroll
+                for (int b = 0; b < B; ++b) base[(size_t)b * nthr] = x[b];
+                if (HAS00 && (int)k == k00) record_origin_deposits<WT>(J.h00, w0 * 32, acc);
+            }
         }
     }
 

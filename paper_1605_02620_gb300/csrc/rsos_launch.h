@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "rsos_device.cuh"
+#include "rsos_persist.cuh"
 
 namespace rsos {
 
@@ -26,6 +27,27 @@ RSOS_DECLARE_SX(2)
 RSOS_DECLARE_SX(4)
 RSOS_DECLARE_SX(8)
 #undef RSOS_DECLARE_SX
+
+// Persistent dataflow engine.  plan_persist fills the block size, chunk
+// width, grid (resident blocks) and phase lag for a job; launch_persist runs
+// the tickets of sweeps [A.t0, A.t0 + n) as one cooperative launch.
+struct PersistPlan {
+    int CW, K, D, nthr, grid;
+    size_t smem;
+};
+cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out);
+cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A,
+                           const PersistPlan& P, cudaStream_t s);
+#define RSOS_DECLARE_PERSIST(SX)                                                                      \
+    cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles,             \
+                                   PersistPlan* out);                                                  \
+    cudaError_t launch_persist_s##SX(const JobDev& J, int words_per_thread, const PersistArgs& A,      \
+                                     const PersistPlan& P, cudaStream_t s);
+RSOS_DECLARE_PERSIST(1)
+RSOS_DECLARE_PERSIST(2)
+RSOS_DECLARE_PERSIST(4)
+RSOS_DECLARE_PERSIST(8)
+#undef RSOS_DECLARE_PERSIST
 
 // Measurement (Eq. 2 numerators), exact: fills rec[S_pad][4] with the 128-bit
 // sum h and sum h^2 of every lane as (lo, hi) int64 pairs.

@@ -11,7 +11,8 @@
 //     sum h^2 = L^2 h00^2 + 2 h00 sum rel + sum rel^2
 // in 128-bit integers.  Kernels:
 //   row0_prefix_kernel   rel(x, 0) for every lane (one block per lane word)
-//   column_walk_kernel   per column and lane, sum rel and sum rel^2 down y
+//   column_walk_kernel   per column and lane, sum rel and sum rel^2 down y,
+//                        in row segments combined exactly in order
 //   finalize_kernel      per lane, 128-bit totals combined with h00
 #include "rsos_launch.h"
 
@@ -38,102 +39,158 @@ __device__ __forceinline__ int residue_diff(int a, int b, int B)
     return d >= (1 << (B - 1)) ? d - (1 << B) : d;
 }
 
+// rel(x, 0) of every lane of word blockIdx.x, in tiles of 1024 sites: thread
+// (lane j, sub-chunk c) sums the differences of 32 consecutive sites, a
+// per-lane scan over the 32 sub-chunks gives the offsets, and the running
+// carry joins the tiles.
 __global__ void __launch_bounds__(1024) row0_prefix_kernel(JobDev J, int32_t* __restrict__ row0)
 {
+    __shared__ uint32_t words[4][1025];
     __shared__ int32_t chunk_sum[32][33];
     const int w = blockIdx.x, lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const int L = J.L, B = J.B;
-    const int per = (L + 31) / 32;
-    const int x0 = min(L, c * per), x1 = min(L, x0 + per);
-    int s = 0;
-    if (x0 < x1) {
-        int vprev = lane_residue(J, x0, 0, w, lane);
-        for (int x = x0; x < x1 && x + 1 < L; ++x) {
-            const int v = lane_residue(J, x + 1, 0, w, lane);
-            s += residue_diff(vprev, v, B);
-            vprev = v;
+    const size_t plane = (size_t)L * L * J.NW;
+    int32_t* out = row0 + (size_t)(w * 32 + lane) * L;
+    int carry = 0;
+    for (int X0 = 0; X0 < L; X0 += 1024) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 1025; k += blockDim.x) {
+            const int x = X0 + k;
+            for (int b = 0; b < B; ++b) words[b][k] = x < L ? J.planes[b * plane + site_word(J, x, 0, w)] : 0u;
         }
-    }
-    chunk_sum[c][lane] = s;
-    __syncthreads();
-    int rel = 0;
-    for (int cc = 0; cc < c; ++cc) rel += chunk_sum[cc][lane];
-    if (x0 < x1) {
-        int32_t* out = row0 + (size_t)(w * 32 + lane) * L;
-        int vprev = lane_residue(J, x0, 0, w, lane);
-        for (int x = x0; x < x1; ++x) {
-            out[x] = rel;
+        __syncthreads();
+        const int i0 = 32 * c;
+        int v = 0;
+        for (int b = 0; b < B; ++b) v |= (int)((words[b][i0] >> lane) & 1u) << b;
+        int loc[32];
+        int acc = 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            loc[i] = acc;
+            const int x = X0 + i0 + i;
             if (x + 1 < L) {
-                const int v = lane_residue(J, x + 1, 0, w, lane);
-                rel += residue_diff(vprev, v, B);
-                vprev = v;
+                int vn = 0;
+                for (int b = 0; b < B; ++b) vn |= (int)((words[b][i0 + i + 1] >> lane) & 1u) << b;
+                acc += residue_diff(v, vn, B);
+                v = vn;
             }
         }
+        chunk_sum[c][lane] = acc;
+        __syncthreads();
+        int off = carry, total = carry;
+        for (int cc = 0; cc < 32; ++cc) {
+            const int sc = chunk_sum[cc][lane];
+            if (cc < c) off += sc;
+            total += sc;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int x = X0 + i0 + i;
+            if (x < L) out[x] = off + loc[i];
+        }
+        carry = total;
     }
 }
 
-// grid (T * ceil(nT/32), NW), 128 threads: 32 columns of one class x 4 groups
-// of 8 lanes of word blockIdx.y.
-__global__ void __launch_bounds__(128) column_walk_kernel(JobDev J, const int32_t* __restrict__ row0,
+// Column sums, exact.  Block (lane group blockIdx.x of 8 lanes, column block
+// blockIdx.y = 32 columns of one class, word blockIdx.z) with 8 warps; warp s
+// walks row segment s of the 32 columns.  Relative to its first row a
+// segment yields, per lane, (Delta, sum r, sum r^2); the segments combine in
+// order:  offset o accumulates the Deltas and a segment of n rows adds
+// n o + sum r  and  n o^2 + 2 o sum r + sum r^2.  Adding rel(x, 0) gives the
+// column totals, which a warp reduction sums over the 32 columns.
+constexpr int kSeg = 8;
+
+__global__ void __launch_bounds__(256) column_walk_kernel(JobDev J, const int32_t* __restrict__ row0,
                                                           int S_pad, int64_t* __restrict__ partial)
 {
-    const int w = blockIdx.y, cb = blockIdx.x;
+    __shared__ int32_t sD[kSeg][8][32];
+    __shared__ int32_t sS1[kSeg][8][32];
+    __shared__ long long sS2[kSeg][8][32];
+    const int lg = blockIdx.x, cb = blockIdx.y, w = blockIdx.z;
     const int T = J.T, nT = J.nT, L = J.L, B = J.B;
     const int u = cb % T;
-    const int m = (cb / T) * 32 + (threadIdx.x & 31);
-    const int lg = threadIdx.x >> 5;
+    const int col = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int m = (cb / T) * 32 + col;
     const bool valid = m < nT;
     const int x = m * T + u;
-    int rel[8], vprev[8];
-    long long s1[8], s2[8];
+    const int RL = (L + kSeg - 1) / kSeg;
+    const int y0 = min(L, seg * RL), y1 = min(L, y0 + RL);
+    int r[8], s1[8], vprev[8];
+    long long s2[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        rel[j] = 0;
-        vprev[j] = 0;
-        s1[j] = 0;
-        s2[j] = 0;
+    for (int k = 0; k < 8; ++k) {
+        r[k] = 0;
+        s1[k] = 0;
+        s2[k] = 0;
+        vprev[k] = 0;
     }
-    if (valid) {
+    if (valid && y0 < y1) {
         const size_t plane = (size_t)L * L * J.NW;
         const size_t row_stride = (size_t)T * nT * J.NW;
-        size_t idx = site_word(J, x, 0, w);
-        uint32_t wv[4];
+        size_t idx = site_word(J, x, y0, w);
+        uint32_t wv[4] = {0u, 0u, 0u, 0u};
         for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int lane = lg * 8 + j;
-            rel[j] = row0[(size_t)(w * 32 + lane) * L + x];
+        for (int k = 0; k < 8; ++k) {
             int v = 0;
-            for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> j) & 1u) << b;
-            vprev[j] = v;
-            s1[j] = rel[j];
-            s2[j] = (long long)rel[j] * rel[j];
+            for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> k) & 1u) << b;
+            vprev[k] = v;
         }
-        for (int y = 1; y < L; ++y) {
+        // rows y0+1 .. y1 (row y1, if inside the lattice, only closes Delta)
+        const int ylast = y1 < L ? y1 : L - 1;
+        for (int y = y0 + 1; y <= ylast; ++y) {
             idx += row_stride;
             for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
+            const bool inside = y < y1;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int k = 0; k < 8; ++k) {
                 int v = 0;
-                for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> j) & 1u) << b;
-                rel[j] += residue_diff(vprev[j], v, B);
-                vprev[j] = v;
-                s1[j] += rel[j];
-                s2[j] += (long long)rel[j] * rel[j];
+                for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> k) & 1u) << b;
+                r[k] += residue_diff(vprev[k], v, B);
+                vprev[k] = v;
+                if (inside) {
+                    s1[k] += r[k];
+                    s2[k] += (long long)r[k] * r[k];
+                }
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        long long a = s1[j], b = s2[j];
-        for (int off = 16; off > 0; off >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, off);
-            b += __shfl_down_sync(0xffffffffu, b, off);
+    for (int k = 0; k < 8; ++k) {
+        sD[seg][k][col] = r[k];
+        sS1[seg][k][col] = s1[k];
+        sS2[seg][k][col] = s2[k];
+    }
+    __syncthreads();
+    if (seg != 0) return;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int lane = lg * 8 + k;
+        long long t1 = 0, t2 = 0;
+        if (valid) {
+            long long off = 0;
+            for (int sg = 0; sg < kSeg; ++sg) {
+                const int a0 = min(L, sg * RL), a1 = min(L, a0 + RL);
+                const long long n = a1 - a0;
+                if (n <= 0) break;
+                const long long sr = sS1[sg][k][col], sr2 = sS2[sg][k][col];
+                t1 += n * off + sr;
+                t2 += n * off * off + 2 * off * sr + sr2;
+                off += sD[sg][k][col];
+            }
+            const long long rel0 = row0[(size_t)(w * 32 + lane) * L + x];
+            t2 += (long long)L * rel0 * rel0 + 2 * rel0 * t1;
+            t1 += (long long)L * rel0;
         }
-        if ((threadIdx.x & 31) == 0) {
-            const size_t r = ((size_t)cb * S_pad + (size_t)w * 32 + lg * 8 + j) * 2;
-            partial[r] = a;
-            partial[r + 1] = b;
+        for (int o = 16; o > 0; o >>= 1) {
+            t1 += __shfl_down_sync(0xffffffffu, t1, o);
+            t2 += __shfl_down_sync(0xffffffffu, t2, o);
+        }
+        if (col == 0) {
+            const size_t rr = ((size_t)cb * S_pad + (size_t)w * 32 + lane) * 2;
+            partial[rr] = t1;
+            partial[rr + 1] = t2;
         }
     }
 }
@@ -170,16 +227,32 @@ __global__ void __launch_bounds__(256) plain_sum_kernel(const int32_t* __restric
     }
 }
 
-__global__ void finalize_kernel(const int64_t* __restrict__ partial, int nrows, int S_pad, int L,
-                                const int64_t* __restrict__ h00, int64_t* __restrict__ rec)
+// Per lane (one block each): 128-bit totals over the partial rows, then the
+// absolute sums with h00.
+__global__ void __launch_bounds__(128) finalize_kernel(const int64_t* __restrict__ partial, int nrows, int S_pad,
+                                                       int L, const int64_t* __restrict__ h00,
+                                                       int64_t* __restrict__ rec)
 {
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    if (lane >= S_pad) return;
+    __shared__ __int128 a1[128], a2[128];
+    const int lane = blockIdx.x;
     __int128 s1 = 0, s2 = 0;
-    for (int r = 0; r < nrows; ++r) {
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
         s1 += (__int128)partial[((size_t)r * S_pad + lane) * 2];
         s2 += (__int128)partial[((size_t)r * S_pad + lane) * 2 + 1];
     }
+    a1[threadIdx.x] = s1;
+    a2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            a1[threadIdx.x] += a1[threadIdx.x + o];
+            a2[threadIdx.x] += a2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    s1 = a1[0];
+    s2 = a2[0];
     const __int128 h0 = h00 ? (__int128)h00[lane] : (__int128)0;
     const __int128 area = (__int128)L * L;
     const __int128 sh = area * h0 + s1;
@@ -234,12 +307,12 @@ cudaError_t launch_measure(const JobDev& J, bool plain, int S_pad, int32_t* row0
     if (ncb > ncb_capacity) return cudaErrorInvalidValue;
     if (plain) {
         plain_sum_kernel<<<ncb, 256, 0, s>>>(J.heights, (long long)J.L * J.L, partial);
-        finalize_kernel<<<1, 32, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec);
+        finalize_kernel<<<1, 128, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec);
         return cudaGetLastError();
     }
     row0_prefix_kernel<<<J.NW, 1024, 0, s>>>(J, row0);
-    column_walk_kernel<<<dim3(ncb, J.NW), 128, 0, s>>>(J, row0, S_pad, partial);
-    finalize_kernel<<<(S_pad + 127) / 128, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec);
+    column_walk_kernel<<<dim3(4, ncb, J.NW), 256, 0, s>>>(J, row0, S_pad, partial);
+    finalize_kernel<<<S_pad, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,145 @@
+// Work order and dependencies of the persistent dataflow engine.
+//
+// The double-tiling sweep (section II) is a sequence of phases; inside a
+// phase all active sub-tiles are independent.  Instead of a grid-wide barrier
+// after every phase, the engine splits each phase into work items
+//     (t, p, r, c) = sweep t, phase p, tile row r of sweep t's tiling,
+//                    chunk c of K consecutive chunks of that row,
+// and lets an item start as soon as the items it conflicts with are done.  An
+// item reads and writes only its sub-tiles and their one-site halos, so
+//   - for p >= 1 it needs phase p-1 of rows r-1, r, r+1 of the same sweep;
+//   - for p == 0 it needs phase 3 of sweep t-1 on every tile row of t-1's
+//     tiling that starts less than T + 2 site rows away from its own tile row
+//     (the tiling moved between the sweeps; footprints reach one site beyond
+//     a tile row).
+// Everything else follows transitively.  Completion is counted per (p, r):
+// done[p][r] reaches (t+1)*K when every chunk of rows r in sweeps <= t is done.
+//
+// Tickets hand the items out in an order in which every dependency precedes
+// its dependants (so the lowest unfinished ticket can always run and the
+// engine cannot deadlock): sweeps in order; inside a sweep, phase p visits
+// tile rows starting at s_t + p, and row j of that visit is placed at slot
+// j + D*p.  The phase lag D keeps dependencies far behind the front of the
+// ticket stream, so items rarely wait, while the rows touched between the
+// phase-0 front and the phase-3 front (3D tile rows) stay resident in L2.
+#pragma once
+#include "philox.cuh"
+
+namespace rsos {
+
+struct SchedGeom {
+    int L, T, nT;  // lattice, tile edge, tile rows
+    int K;         // chunks per tile row
+    int D;         // phase lag in slots
+    int phase_order;
+    uint32_t seed_lo, seed_hi;
+};
+
+struct Item {
+    uint32_t t;
+    int p, r, c;
+};
+
+struct Dep {
+    int p, r;
+    uint64_t target;  // done[p][r] must reach this value
+};
+
+RSOS_HD int mod_pos(int a, int n)
+{
+    const int m = a % n;
+    return m < 0 ? m + n : m;
+}
+
+// a mod n for a in [-n, 2n): conditional adds instead of a division.
+RSOS_HD int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Tile row where sweep t's phase 0 starts: the row holding site row 64 t
+// (mod L).  Consecutive sweeps start 64 site rows apart, so a new sweep
+// begins where the previous one finished its first rows long ago.
+// TT > 0 is the tile edge known at compile time (g.T otherwise).
+template <int TT = 0>
+RSOS_HD int sweep_start_row(const SchedGeom& g, uint32_t t, int oy)
+{
+    const int T = TT > 0 ? TT : g.T;
+    const int y = (int)((uint32_t)((uint64_t)(t % (uint32_t)g.L) * 64u % (uint32_t)g.L));
+    return wrap1(y - oy, g.L) / T;
+}
+
+// Slot-ordered list of (p, j, c) of one sweep: entry = p | j << 2 | c << 20.
+// Host only.  Returns the number of entries (4 * nT * K).
+inline int build_order_table(int nT, int K, int D, uint32_t* out)
+{
+    int n = 0;
+    const int slots = nT + 3 * D;
+    for (int s = 0; s < slots; ++s)
+        for (int p = 0; p < 4; ++p) {
+            const int j = s - D * p;
+            if (j < 0 || j >= nT) continue;
+            for (int c = 0; c < K; ++c) out[n++] = (uint32_t)p | ((uint32_t)j << 2) | ((uint32_t)c << 20);
+        }
+    return n;
+}
+
+// Item of a ticket; tickets of one launch are 32-bit (launches are split).
+template <int TT = 0>
+RSOS_HD Item item_of_ticket(const SchedGeom& g, const uint32_t* table, uint64_t ticket, uint32_t t0)
+{
+    const uint32_t per_sweep = 4u * (uint32_t)g.nT * (uint32_t)g.K;
+    const uint32_t tk = (uint32_t)ticket;
+    const uint32_t sw = tk / per_sweep;
+    Item it;
+    it.t = t0 + sw;
+    const uint32_t e = table[tk - sw * per_sweep];
+    it.p = (int)(e & 3u);
+    const int j = (int)((e >> 2) & 0x3FFFFu);
+    it.c = (int)(e >> 20);
+    const int T = TT > 0 ? TT : g.T;
+    const Control ctl = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order);
+    int r = sweep_start_row<TT>(g, it.t, ctl.oy) + it.p + j;  // <= 2 nT + 1
+    r = r >= g.nT ? r - g.nT : r;
+    r = r >= g.nT ? r - g.nT : r;
+    it.r = g.nT >= 2 ? r : 0;
+    return it;
+}
+
+// Dependencies of an item; returns their number (<= 4).
+template <int TT = 0>
+RSOS_HD int item_deps(const SchedGeom& g, const Item& it, Dep* out)
+{
+    int n = 0;
+    const int T = TT > 0 ? TT : g.T;
+    if (it.p > 0) {
+        const uint64_t target = ((uint64_t)it.t + 1) * (uint64_t)g.K;
+        const int lo = g.nT >= 3 ? -1 : 0, hi = g.nT >= 3 ? 1 : g.nT - 1;
+        for (int d = lo; d <= hi; ++d) {
+            const int r = wrap1(it.r + d, g.nT);
+            bool dup = false;
+            for (int k = 0; k < n; ++k) dup |= out[k].r == r;
+            if (!dup) out[n++] = Dep{it.p - 1, r, target};
+        }
+        return n;
+    }
+    if (it.t == 0) return 0;
+    const int oy_now = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order).oy;
+    const int oy_prev = sweep_control(g.seed_lo, g.seed_hi, it.t - 1, T, T, g.phase_order).oy;
+    // Rows r' of the previous tiling whose first site row oy_prev + r' T lies
+    // in (y0 - T - 2, y0 + T + 2), y0 = first site row of this tile row: the
+    // offsets y0 + dy, dy in [-(T+1), T+1], that are multiples of T from oy_prev.
+    const uint64_t target = (uint64_t)it.t * (uint64_t)g.K;
+    const int base = it.r * T + oy_now - oy_prev;  // y0 - oy_prev, in (-T, L + T)
+    // smallest dy >= -(T+1) with base + dy = 0 mod T
+    int dy = -(T + 1);
+    int rem = (base + dy) % T;
+    if (rem < 0) rem += T;
+    if (rem) dy += T - rem;
+    for (; dy <= T + 1; dy += T) {
+        const int r = mod_pos((base + dy) / T, g.nT);  // base + dy is a multiple of T
+        bool dup = false;
+        for (int k = 0; k < n; ++k) dup |= out[k].r == r;
+        if (!dup && n < 4) out[n++] = Dep{3, r, target};
+    }
+    return n;
+}
+
+}  // namespace rsos

@@ -57,12 +57,12 @@ cudaError_t launch_phase_t(const JobDev& J, uint32_t t, int p, int q, int ox, in
     const long long total = (long long)J.nT * J.nT * J.NWP;
     const int nthr = pick_threads(per_thread, smem_budget, total);
     const size_t smem = per_thread * nthr;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(phase_kernel<N, WT, SX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(phase_kernel<N, WT, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = smem;
     }
     const long long blocks = (total + nthr - 1) / nthr;
     phase_kernel<N, WT, SX><<<(unsigned)blocks, nthr, smem, s>>>(J, t, p, q, ox, oy, o);
@@ -99,15 +99,16 @@ cudaError_t launch_plain_sx(const JobDev& J, uint32_t t, int p, int q, int ox, i
     const size_t per_thread = (size_t)(SX + 2) * (SX + 2) * sizeof(int32_t);
     const long long total = (long long)J.nT * J.nT;
     const int nthr = pick_threads(per_thread, smem_budget, total);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(plain_phase_kernel<SX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    const size_t smem = per_thread * nthr;
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(plain_phase_kernel<SX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = smem;
     }
     const long long blocks = (total + nthr - 1) / nthr;
-    plain_phase_kernel<SX><<<(unsigned)blocks, nthr, per_thread * nthr, s>>>(J, t, p, q, ox, oy);
+    plain_phase_kernel<SX><<<(unsigned)blocks, nthr, smem, s>>>(J, t, p, q, ox, oy);
     return cudaGetLastError();
 }
 

@@ -72,3 +72,37 @@ uint64_t probe_step(int N, const int* xr, const int* er, const int* wr, const in
 
 int probe_bits(int N) { return rsos::bits_for_step(N); }
 }
+
+// Scheduling rules of the persistent engine.
+#include "rsos_sched.cuh"
+
+extern "C" {
+
+static rsos::SchedGeom make_geom(const int* g8)
+{
+    rsos::SchedGeom g;
+    g.L = g8[0]; g.T = g8[1]; g.nT = g8[0] / g8[1]; g.K = g8[2]; g.D = g8[3]; g.phase_order = g8[4];
+    g.seed_lo = (uint32_t)g8[5]; g.seed_hi = (uint32_t)g8[6];
+    return g;
+}
+
+int probe_order_table(int nT, int K, int D, uint32_t* out) { return rsos::build_order_table(nT, K, D, out); }
+
+void probe_item(const int* g8, const uint32_t* table, uint64_t ticket, uint32_t t0, int* out4)
+{
+    const rsos::Item it = rsos::item_of_ticket<0>(make_geom(g8), table, ticket, t0);
+    out4[0] = (int)it.t; out4[1] = it.p; out4[2] = it.r; out4[3] = it.c;
+}
+
+int probe_deps(const int* g8, const int* item4, int64_t* out12)
+{
+    rsos::Item it;
+    it.t = (uint32_t)item4[0]; it.p = item4[1]; it.r = item4[2]; it.c = item4[3];
+    rsos::Dep d[4];
+    const int n = rsos::item_deps<0>(make_geom(g8), it, d);
+    for (int k = 0; k < n; ++k) {
+        out12[3 * k] = d[k].p; out12[3 * k + 1] = d[k].r; out12[3 * k + 2] = (int64_t)d[k].target;
+    }
+    return n;
+}
+}
