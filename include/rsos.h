@@ -140,6 +140,35 @@ int rsos_selftest_timeout(rsos_handle* h, int64_t budget_ns, void* stream);
  * sweeps, measurements); for accounting and benchmarks. */
 int rsos_launches(const rsos_handle* h, int64_t* out);
 
+/* Width measurement that allocates nothing (no counterpart in the paper).
+ * For callers that cannot allocate device memory when they need a width:
+ * code under a fixed memory budget handed out once (an arena owned by another
+ * framework), real-time loops where an allocation would synchronise the
+ * device, or jobs whose caller-owned buffer holds only the lattice.  Computes
+ * the same exact per-surface sums as rsos_width for a multisurface lattice
+ * (surfaces >= 2) given by device pointers:
+ *   params  the job's parameters (as passed to rsos_init);
+ *   planes  the coded lattice; in a caller-owned rsos_init buffer it starts at
+ *           offset 0;
+ *   h00     the surfaces' absolute heights of site (0,0) (int64 each); in a
+ *           caller-owned buffer at offset B*L*L*ceil(S/32)*4 rounded up to a
+ *           multiple of 256, B = ceil(log2(2N+1));
+ *   sums    device output, surfaces x 4 int64: sum h (low, high 64 bits) and
+ *           sum h^2 (low, high) as two's-complement 128-bit integers.
+ * Queued on stream, asynchronous; calls no cudaMalloc or cudaFree.  Scratch is
+ * one file-scope device array of RSOS_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until the process exits; lattices whose
+ * measurement needs more (about 4*L*32*ceil(S/32) bytes plus per-column sums)
+ * get RSOS_ERANGE.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * (different streams or host threads) race and must be serialised by the
+ * caller.  RSOS_EINVAL for invalid params, NULL pointers or a single-surface
+ * job, RSOS_ECUDA if a CUDA call fails. */
+#define RSOS_NOALLOC_SCRATCH_BYTES (8u << 20)
+int rsos_width_noalloc(const rsos_params* params, const uint32_t* planes, const int64_t* h00, int64_t* sums,
+                       void* stream);
+
 /* Current time of the handle (completed sweeps). */
 int rsos_time(const rsos_handle* h, int64_t* t_out);
 

@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "RsosError", "rsos_params", "rsos_required_bytes", "rsos_init", "rsos_sweep", "rsos_width",
     "rsos_schedule", "rsos_read_series", "rsos_heights", "rsos_time", "rsos_free", "rsos_strerror",
-    "rsos_selftest_timeout", "rsos_launches",
+    "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "library_path",
 ]
@@ -86,6 +86,7 @@ def _load():
             "rsos_time": [vp, P(i64)],
             "rsos_selftest_timeout": [vp, i64, vp],
             "rsos_launches": [vp, P(i64)],
+            "rsos_width_noalloc": [P(rsos_params), vp, vp, vp, vp],
             "rsos_free": [vp],
             "rsos_last_cuda_error": [vp],
             "rsos_batch_create": [P(rsos_params), P(i64), i32, sz, P(vp)],
@@ -199,6 +200,14 @@ def rsos_selftest_timeout(h, budget_ns: int, stream=None) -> int:
     the status (RSOS_ETIMEOUT when the device reported the expiry)."""
     return _check(_load().rsos_selftest_timeout(h, int(budget_ns), _stream(stream)), "rsos_selftest_timeout",
                   allow=(RSOS_ETIMEOUT,))
+
+
+def rsos_width_noalloc(params: rsos_params, planes: int, h00: int, sums: int, stream=None) -> None:
+    """Exact sums of a multisurface lattice given by device addresses, without
+    any allocation (for callers that cannot allocate; see include/rsos.h).
+    ``sums`` is a device address of surfaces x 4 int64 (128-bit sum h, sum h^2)."""
+    _check(_load().rsos_width_noalloc(ctypes.byref(params), ctypes.c_void_p(int(planes)), ctypes.c_void_p(int(h00)),
+                                      ctypes.c_void_p(int(sums)), _stream(stream)), "rsos_width_noalloc")
 
 
 def rsos_launches(h) -> int:
