@@ -276,6 +276,99 @@ def cpu_baseline(L, N, T, seed, target_s: float = 12.0):
             "sample": f"{done} DT sweep(s) of L={L}, N={N}, {cores} lanes (one per thread) from the flat start"}
 
 
+def run_batched(args):
+    """Batched workload: 256 independent jobs (L uniform in {256..4096}, N in
+    {1, 2}, 64 surfaces, t_max log-uniform in [1e3, 1e4] sweeps, seeds =
+    job index), one multi-job persistent launch per class, captured in a CUDA
+    graph; each job's width is measured exactly at its t_max.  One step = the
+    whole batch."""
+    import torch
+
+    import paper_1605_02620_gb300 as R
+    from paper_1605_02620_gb300.inputs import batched_jobs
+
+    scale = args.batch_scale
+    jobs = batched_jobs()
+    params = [R.rsos_params(L=j["L"], N=j["N"], surfaces=j["surfaces"], tile=8, seed=j["seed"], series_capacity=2)
+              for j in jobs]
+    tmax = [max(1, j["t_max"] // scale) for j in jobs]
+    attempts = float(sum(j["L"] * j["L"] * j["surfaces"] * t for j, t in zip(jobs, tmax)))
+    stream = torch.cuda.Stream()
+
+    def one_batch(tm=None):
+        b = R.rsos_batch_create(params, tm or tmax)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        R.rsos_batch_run(b, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        done = set()
+        while len(done) < len(jobs):
+            _, ids = R.rsos_batch_poll(b)
+            done |= set(ids)
+        w2 = [float(R.rsos_read_series(R.rsos_batch_job(b, k), jobs[k]["surfaces"], 2)[3][-1].mean())
+              for k in range(0, len(jobs), 64)]
+        R.rsos_batch_free(b)
+        return ev0.elapsed_time(ev1), w2
+
+    # warm-up: the same batch with t_max / 100 (compiles plans, warms clocks)
+    warm_tmax = [max(1, t // 100) for t in tmax]
+    for _ in range(args.warmup):
+        one_batch(warm_tmax)
+    clocks = ClockSampler(0)
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        ms, w2 = one_batch()
+        total_ms += ms
+    clk = clocks.stop()
+    value = attempts * args.steps / (total_ms / 1e3)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 (bit-sliced int)", "data": "synthetic",
+        "config": {"workload": f"batched: 256 jobs, L in {{256..4096}}, N in {{1,2}}, 64 surfaces, t_max in "
+                               f"[1e3,1e4]/{scale} sweeps, PCG64 seed 2016; one multi-job persistent launch per class "
+                               "in a CUDA graph", "jobs": len(jobs), "attempts_per_step": attempts,
+                   "l2": "inputs larger than L2"},
+        "clocks": clk, "w2_sample": w2,
+    }), flush=True)
+
+
+def run_served(args):
+    """Served workload: a Poisson stream of requests (L = 2^e, e in 8..13, N in
+    1..4, 64 surfaces, t_max log-uniform in [1e2, 1e4] sweeps, PCG64 seed
+    2017) admitted under an HBM budget by the continuous-batching server.
+    --serve-jobs / --serve-scale (t_max divisor) / --serve-rate (arrivals per
+    second) bound the run; the JSON line states them."""
+    import torch
+
+    from paper_1605_02620_gb300.inputs import served_jobs
+    from paper_1605_02620_gb300.serve import Request, Server
+
+    jobs = served_jobs(n_jobs=args.serve_jobs, rate=args.serve_rate)
+    reqs = [Request(L=j["L"], N=j["N"], t_max=max(1, j["t_max"] // args.serve_scale), seed=j["seed"],
+                    surfaces=j["surfaces"], arrival=j["arrival"], rid=k) for k, j in enumerate(jobs)]
+    stream = torch.cuda.Stream()
+    warm = [Request(L=256, N=n, t_max=20, seed=k, surfaces=64, arrival=0.0, rid=k) for k, n in enumerate((1, 2, 3, 4))]
+    Server(hbm_budget=args.serve_budget, stream=stream).run(warm)
+    clocks = ClockSampler(0)
+    clocks.start()
+    rep = Server(hbm_budget=args.serve_budget, epoch_s=args.serve_epoch, stream=stream).run(reqs)
+    clk = clocks.stop()
+    s = rep.summary()
+    print(json.dumps({
+        "metric": METRIC, "value": s["attempts_per_s"], "unit": "attempts/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": rep.wall_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64/u32 (bit-sliced int)", "data": "synthetic",
+        "config": {"workload": f"served: {len(reqs)} Poisson requests at {args.serve_rate}/s, L=2^(8..13), N in 1..4, "
+                               f"64 surfaces, t_max in [1e2,1e4]/{args.serve_scale} sweeps, PCG64 seed 2017",
+                   "hbm_budget": args.serve_budget, "epoch_s": args.serve_epoch},
+        "serve": s, "clocks": clk,
+    }), flush=True)
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,6 +409,14 @@ def main():
                     help="sweeps per job (reduced values only for profiling captures)")
     ap.add_argument("--measurements", type=int, default=WORKLOAD["measurements"],
                     help="measurement times per job (reduced values only for profiling captures)")
+    ap.add_argument("--workload", default="ms-n1", choices=["ms-n1", "batched", "served"])
+    ap.add_argument("--batch-scale", type=int, default=1,
+                    help="divide the batched jobs' t_max by this factor (profiling / quick checks)")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-scale", type=int, default=1)
+    ap.add_argument("--serve-budget", type=int, default=200 << 30)
+    ap.add_argument("--serve-epoch", type=float, default=0.02)
     ap.add_argument("--quick", action="store_true",
                     help="profiling capture: timed steps only (no kernel timing, e2e or CPU baseline)")
     args = ap.parse_args()
@@ -326,6 +427,10 @@ def main():
                                  " for profiling]")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_gpu(args)
 

@@ -183,6 +183,17 @@ const char* rsos_strerror(int status);
  * h == NULL, the CUDA error of the last failed rsos_init on this thread. */
 int rsos_last_cuda_error(const rsos_handle* h);
 
+/* Advance several independent jobs together to their targets (t_target[i] >=
+ * the job's time): multisurface jobs of equal N, word width and tile share one
+ * persistent launch per class (the warps crowd onto as few jobs as keep them
+ * busy), stopping at every scheduled measurement time on the way; other jobs
+ * run through rsos_sweep.  Results are bit-identical to advancing each job
+ * alone.  Synchronises the stream (the continuous-batching primitive of a
+ * serving loop: admit and retire jobs between calls).  RSOS_EINVAL for a NULL
+ * or repeated handle or a target before the job's time, RSOS_ETIMEOUT if a
+ * device wait gave up. */
+int rsos_advance(rsos_handle* const* jobs, const int64_t* t_target, int32_t n, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batches: many independent jobs of different L and N advanced together by
  * one persistent dataflow kernel (captured in a CUDA graph), each to its own

@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "RsosError", "rsos_params", "rsos_required_bytes", "rsos_init", "rsos_sweep", "rsos_width",
     "rsos_schedule", "rsos_read_series", "rsos_heights", "rsos_time", "rsos_free", "rsos_strerror",
-    "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc",
+    "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc", "rsos_advance",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "library_path",
 ]
@@ -87,6 +87,7 @@ def _load():
             "rsos_selftest_timeout": [vp, i64, vp],
             "rsos_launches": [vp, P(i64)],
             "rsos_width_noalloc": [P(rsos_params), vp, vp, vp, vp],
+            "rsos_advance": [P(vp), P(i64), i32, vp],
             "rsos_free": [vp],
             "rsos_last_cuda_error": [vp],
             "rsos_batch_create": [P(rsos_params), P(i64), i32, sz, P(vp)],
@@ -210,6 +211,17 @@ def rsos_width_noalloc(params: rsos_params, planes: int, h00: int, sums: int, st
                                       ctypes.c_void_p(int(sums)), _stream(stream)), "rsos_width_noalloc")
 
 
+def rsos_advance(handles, targets, stream=None) -> None:
+    """Advance several jobs together to their target times (one multi-job
+    persistent launch per class; synchronises the stream)."""
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    tg = np.ascontiguousarray(targets, dtype=np.int64)
+    rc = _load().rsos_advance(arr, _p(tg, ctypes.c_int64), n, _stream(stream))
+    if rc != RSOS_OK:
+        raise RsosError(rc, "rsos_advance", _load().rsos_last_cuda_error(None) if rc == RSOS_ECUDA else 0)
+
+
 def rsos_launches(h) -> int:
     n = ctypes.c_int64()
     _check(_load().rsos_launches(h, ctypes.byref(n)), "rsos_launches")
@@ -246,15 +258,18 @@ def rsos_batch_schedule(b, job: int, times) -> None:
 
 
 def rsos_batch_run(b, stream=None) -> None:
-    _check(_load().rsos_batch_run(b, _stream(stream)), "rsos_batch_run")
+    rc = _load().rsos_batch_run(b, _stream(stream))
+    if rc != RSOS_OK:
+        raise RsosError(rc, "rsos_batch_run", _load().rsos_last_cuda_error(None) if rc == RSOS_ECUDA else 0)
 
 
 def rsos_batch_poll(b, cap: int = 4096):
     """Returns (status, finished job ids); status is RSOS_OK or RSOS_EBUSY."""
     ids = np.zeros(max(cap, 1), dtype=np.int32)
     n = ctypes.c_int32()
-    rc = _check(_load().rsos_batch_poll(b, _p(ids, ctypes.c_int32), int(cap), ctypes.byref(n)),
-                "rsos_batch_poll", allow=(RSOS_EBUSY,))
+    rc = _load().rsos_batch_poll(b, _p(ids, ctypes.c_int32), int(cap), ctypes.byref(n))
+    if rc not in (RSOS_OK, RSOS_EBUSY):
+        raise RsosError(rc, "rsos_batch_poll", _load().rsos_last_cuda_error(None) if rc == RSOS_ECUDA else 0)
     return rc, [int(v) for v in ids[:n.value]]
 
 

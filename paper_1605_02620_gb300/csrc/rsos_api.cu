@@ -342,6 +342,29 @@ cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const 
     }
 }
 
+cudaError_t plan_multi(int N, int SX, int words_per_thread, int* grid, int* block, size_t* smem)
+{
+    switch (SX) {
+        case 1: return plan_multi_s1(N, words_per_thread, grid, block, smem);
+        case 2: return plan_multi_s2(N, words_per_thread, grid, block, smem);
+        case 4: return plan_multi_s4(N, words_per_thread, grid, block, smem);
+        case 8: return plan_multi_s8(N, words_per_thread, grid, block, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_multi(int N, int SX, int words_per_thread, const MultiArgs& M, int grid, int block, size_t smem,
+                         cudaStream_t s)
+{
+    switch (SX) {
+        case 1: return launch_multi_s1(N, words_per_thread, M, grid, block, smem, s);
+        case 2: return launch_multi_s2(N, words_per_thread, M, grid, block, smem, s);
+        case 4: return launch_multi_s4(N, words_per_thread, M, grid, block, smem, s);
+        case 8: return launch_multi_s8(N, words_per_thread, M, grid, block, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out)
 {
     switch (SX) {
@@ -651,5 +674,466 @@ const char* rsos_strerror(int status)
 }
 
 int rsos_last_cuda_error(const rsos_handle* h) { return h ? h->cuda_err : g_init_cuda_err; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Multi-job execution (rsos_advance and batches).  Jobs are grouped into
+// classes of equal (N, word width, tile edge); per round one multi-job
+// persistent launch per class advances every member to its next stop (a
+// measurement time or its target), then the members due for a measurement
+// are measured.  Jobs outside the persistent engine run through rsos_sweep.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchClass {
+    int N, NWT, SX;
+    std::vector<int> members;          // indices into MultiWork::jobs
+    rsos::MultiJob* d_jobs;            // [rounds][members]
+    unsigned long long* d_tickets;     // [members] tickets handed out, then [members] items finished
+    unsigned int* d_first;             // 1
+    unsigned int* d_exhausted;         // [members]
+    unsigned int* d_err;               // 1
+    int grid, block;
+    size_t smem;
+};
+
+struct MultiWork {
+    std::vector<rsos_handle*> jobs;
+    std::vector<int64_t> target;
+    std::vector<std::vector<int64_t>> stops;  // per job: ascending stop times, last = target
+    std::vector<BatchClass> classes;
+    std::vector<int> solo;
+    size_t rounds = 0, per_round_jobs = 0;
+    void* d_block = nullptr;           // class state
+    void* d_tables = nullptr;          // job tables of all rounds
+    rsos::MultiJob* h_jobs = nullptr;  // pinned staging of the job tables
+    unsigned int* h_err = nullptr;     // pinned: error word of each class after its last launch
+};
+
+void multi_release(MultiWork& w)
+{
+    if (w.d_tables) cudaFree(w.d_tables);
+    if (w.d_block) cudaFree(w.d_block);
+    if (w.h_jobs) cudaFreeHost(w.h_jobs);
+    if (w.h_err) cudaFreeHost(w.h_err);
+    w.d_tables = w.d_block = nullptr;
+    w.h_jobs = nullptr;
+    w.h_err = nullptr;
+}
+
+// Classes, launch plans, member order and all device / pinned buffers (no
+// allocation happens later, so multi_enqueue can be captured in a graph).
+int multi_prepare(MultiWork& w)
+{
+    for (size_t i = 0; i < w.jobs.size(); ++i) {
+        rsos_handle* h = w.jobs[i];
+        if (!h->persist) {
+            w.solo.push_back((int)i);
+            continue;
+        }
+        bool placed = false;
+        for (BatchClass& c : w.classes)
+            if (c.N == h->p.N && c.NWT == h->NWT && c.SX == h->SX) {
+                c.members.push_back((int)i);
+                placed = true;
+                break;
+            }
+        if (!placed) {
+            BatchClass c{};
+            c.N = h->p.N;
+            c.NWT = h->NWT;
+            c.SX = h->SX;
+            c.members.push_back((int)i);
+            w.classes.push_back(c);
+        }
+    }
+    // Members in decreasing lattice size (then target): the tail of a class is
+    // many small jobs, which run side by side.
+    for (BatchClass& c : w.classes)
+        std::stable_sort(c.members.begin(), c.members.end(), [&](int x, int y) {
+            const int64_t lx = w.jobs[x]->p.L, ly = w.jobs[y]->p.L;
+            return lx != ly ? lx > ly : w.target[x] > w.target[y];
+        });
+    size_t dev_bytes = 0;
+    for (BatchClass& c : w.classes) {
+        if (rsos::plan_multi(c.N, c.SX, c.NWT, &c.grid, &c.block, &c.smem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return RSOS_ECUDA;
+        }
+        dev_bytes += align256(2 * c.members.size() * 8) + 256 + align256(c.members.size() * 4) + 256;
+        w.per_round_jobs += c.members.size();
+        for (int i : c.members) w.rounds = std::max(w.rounds, w.stops[i].size());
+    }
+    if (w.classes.empty()) return RSOS_OK;
+    if (cudaMalloc(&w.d_block, dev_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        w.d_block = nullptr;
+        return RSOS_ENOMEM;
+    }
+    const size_t entries = w.per_round_jobs * w.rounds;
+    if (cudaMalloc(&w.d_tables, entries * sizeof(rsos::MultiJob)) != cudaSuccess ||
+        cudaHostAlloc((void**)&w.h_jobs, entries * sizeof(rsos::MultiJob), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&w.h_err, w.classes.size() * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RSOS_ENOMEM;
+    }
+    unsigned char* cur = static_cast<unsigned char*>(w.d_block);
+    rsos::MultiJob* dj = static_cast<rsos::MultiJob*>(w.d_tables);
+    for (size_t ci = 0; ci < w.classes.size(); ++ci) {
+        BatchClass& c = w.classes[ci];
+        const size_t m = c.members.size();
+        c.d_tickets = reinterpret_cast<unsigned long long*>(cur);
+        cur += align256(2 * m * 8);
+        c.d_first = reinterpret_cast<unsigned int*>(cur);
+        c.d_err = reinterpret_cast<unsigned int*>(cur + 8);
+        cur += 256;
+        c.d_exhausted = reinterpret_cast<unsigned int*>(cur);
+        cur += align256(m * 4) + 256;
+        c.d_jobs = dj;
+        dj += m * w.rounds;
+        w.h_err[ci] = 0;
+    }
+    return RSOS_OK;
+}
+
+// Completion event of a job; under stream capture it must become an external
+// event node of the graph so that the host can query it after the launch.
+cudaError_t record_done(cudaEvent_t ev, cudaStream_t s, bool capturing)
+{
+    return capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+}
+
+// Queue all rounds on stream s (no allocation: capturable).  done (nullable)
+// gets each job's completion event.
+int multi_enqueue(MultiWork& w, cudaStream_t s, bool capturing, const std::vector<cudaEvent_t>* done)
+{
+    for (int i : w.solo) {
+        rsos_handle* h = w.jobs[i];
+        const int rc = rsos_sweep(h, w.target[i] - h->t, s);
+        if (rc) return rc;
+        if (done && record_done((*done)[i], s, capturing) != cudaSuccess) return RSOS_ECUDA;
+    }
+    if (w.classes.empty()) return RSOS_OK;
+    for (const BatchClass& c : w.classes)
+        for (int i : c.members) {
+            rsos_handle* h = w.jobs[i];
+            size_t due = 0;
+            for (size_t k = h->sched_pos; k < h->sched.size() && h->sched[k] <= w.target[i]; ++k) ++due;
+            if (h->series_t.size() + due > (size_t)h->cap) return RSOS_ERANGE;
+        }
+    for (BatchClass& c : w.classes)
+        if (rsos::launch_zero(c.d_err, 4, s) != cudaSuccess) return RSOS_ECUDA;
+    for (size_t r = 0; r < w.rounds; ++r) {
+        size_t off = 0;
+        for (size_t ci = 0; ci < w.classes.size(); ++ci) {
+            BatchClass& c = w.classes[ci];
+            rsos::MultiJob* row = w.h_jobs + r * w.per_round_jobs + off;
+            off += c.members.size();
+            bool any = false;
+            for (size_t m = 0; m < c.members.size(); ++m) {
+                const int i = c.members[m];
+                rsos_handle* h = w.jobs[i];
+                int64_t stop = h->t;
+                if (r < w.stops[i].size()) stop = std::max<int64_t>(h->t, w.stops[i][r]);
+                const int64_t per_sweep = 4ll * h->J.nT * h->plan.K;
+                if ((stop - h->t) * per_sweep >= ((int64_t)1 << 31)) return RSOS_ERANGE;
+                const rsos::PersistArgs a = persist_args(h, (uint32_t)h->t, stop - h->t);
+                rsos::MultiJob& mj = row[m];
+                mj.J = a.J;
+                mj.G = a.G;
+                mj.table = a.table;
+                mj.done = a.done;
+                mj.ticket = c.d_tickets + m;
+                mj.finished = c.d_tickets + c.members.size() + m;
+                mj.n_tickets = a.n_tickets;
+                // in-flight cap: two thirds of the tickets between an item and
+                // its dependencies ((D - 2) slots of 4K items)
+                mj.cap = (unsigned long long)std::max<int64_t>(32, (int64_t)(h->plan.D - 2) * 4 * h->plan.K * 2 / 3);
+                mj.t0 = a.t0;
+                mj.CW = a.CW;
+                mj.TPL = a.TPL;
+                mj.pad_ = 0;
+                any |= a.n_tickets > 0;
+                h->t = stop;
+            }
+            if (any) {
+                rsos::MultiJob* dj = c.d_jobs + r * c.members.size();
+                cudaError_t e =
+                    cudaMemcpyAsync(dj, row, c.members.size() * sizeof(rsos::MultiJob), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = rsos::launch_zero(c.d_tickets, 2 * c.members.size() * 8, s);
+                if (e == cudaSuccess) e = rsos::launch_zero(c.d_first, 4, s);
+                if (e == cudaSuccess) e = rsos::launch_zero(c.d_exhausted, c.members.size() * 4, s);
+                rsos::MultiArgs M;
+                M.jobs = dj;
+                M.n_jobs = (int)c.members.size();
+                M.first = c.d_first;
+                M.exhausted = c.d_exhausted;
+                M.err = c.d_err;
+                M.budget_ns = 1000000000ll;
+                if (e == cudaSuccess) e = rsos::launch_multi(c.N, c.SX, c.NWT, M, c.grid, c.block, c.smem, s);
+                if (e != cudaSuccess) return RSOS_ECUDA;
+            }
+            for (int i : c.members) {
+                rsos_handle* h = w.jobs[i];
+                if (any) h->launches += 5;
+                const int rc = measure_due(h, s);
+                if (rc) return rc;
+            }
+        }
+        for (size_t ci = 0; ci < w.classes.size(); ++ci)
+            for (int i : w.classes[ci].members)
+                if (w.stops[i].size() == r + 1) {
+                    if (cudaMemcpyAsync(&w.h_err[ci], w.classes[ci].d_err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                        return RSOS_ECUDA;
+                    if (done && record_done((*done)[i], s, capturing) != cudaSuccess) return RSOS_ECUDA;
+                }
+    }
+    return RSOS_OK;
+}
+
+// Stops of job h on the way to target: its pending schedule times, then target.
+std::vector<int64_t> stops_of(const rsos_handle* h, int64_t target)
+{
+    std::vector<int64_t> out;
+    for (size_t k = h->sched_pos; k < h->sched.size(); ++k)
+        if (h->sched[k] > h->t && h->sched[k] < target) out.push_back(h->sched[k]);
+    out.push_back(target);
+    return out;
+}
+
+}  // namespace
+
+extern "C" int rsos_advance(rsos_handle* const* jobs, const int64_t* t_target, int32_t n, void* stream)
+{
+    if (!jobs || !t_target || n < 1) return RSOS_EINVAL;
+    MultiWork w;
+    for (int32_t i = 0; i < n; ++i) {
+        rsos_handle* h = jobs[i];
+        if (!h || t_target[i] < h->t || t_target[i] > kMaxSweeps) return RSOS_EINVAL;
+        if (h->sticky) return h->sticky;
+        for (int32_t k = 0; k < i; ++k)
+            if (jobs[k] == h) return RSOS_EINVAL;
+        w.jobs.push_back(h);
+        w.target.push_back(t_target[i]);
+        w.stops.push_back(stops_of(h, t_target[i]));
+    }
+    cudaStream_t s = as_stream(stream);
+    for (rsos_handle* h : w.jobs) {
+        const int rc = measure_due(h, s);  // a measurement due at the current time
+        if (rc) return rc;
+    }
+    int rc = multi_prepare(w);
+    if (rc == RSOS_OK) rc = multi_enqueue(w, s, false, nullptr);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (rc == RSOS_OK && e != cudaSuccess) rc = RSOS_ECUDA;
+    if (rc == RSOS_OK)
+        for (size_t ci = 0; ci < w.classes.size(); ++ci)
+            if (w.h_err[ci]) rc = RSOS_ETIMEOUT;
+    if (rc == RSOS_ECUDA) g_init_cuda_err = (int)(e != cudaSuccess ? e : cudaGetLastError());
+    multi_release(w);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batches (include/rsos.h): a MultiWork over jobs the batch owns, with each
+// job's schedule as its stops, captured in one CUDA graph.
+// ---------------------------------------------------------------------------
+struct rsos_batch {
+    MultiWork w;
+    std::vector<int64_t> t_max;
+    std::vector<std::vector<int64_t>> sched;
+    std::vector<cudaEvent_t> done;
+    std::vector<char> reported;
+    bool prepared;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool queued;
+    int status;
+};
+
+extern "C" {
+
+int rsos_batch_free(rsos_batch* b);
+
+int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n_jobs, size_t hbm_budget,
+                      rsos_batch** out)
+{
+    if (!out) return RSOS_EINVAL;
+    *out = nullptr;
+    if (!params || !t_max || n_jobs < 1) return RSOS_EINVAL;
+    std::vector<rsos_params> ps(params, params + n_jobs);
+    size_t total = 0;
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        if (t_max[i] < 0 || t_max[i] > kMaxSweeps) return RSOS_EINVAL;
+        if (ps[i].surfaces > 1 && ps[i].engine == 0) {
+            const int NW = (ps[i].surfaces + 31) / 32;
+            if (NW / words_per_thread(NW) <= 32) ps[i].engine = 2;
+        }
+        size_t bytes = 0;
+        const int rc = rsos_required_bytes(&ps[i], &bytes);
+        if (rc) return rc;
+        total += bytes;
+    }
+    if (hbm_budget && total > hbm_budget) return RSOS_ENOMEM;
+    rsos_batch* b = new (std::nothrow) rsos_batch();
+    if (!b) return RSOS_ENOMEM;
+    b->prepared = false;
+    b->graph = nullptr;
+    b->exec = nullptr;
+    b->queued = false;
+    b->status = RSOS_OK;
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        rsos_handle* h = nullptr;
+        const int rc = rsos_init(&ps[i], nullptr, 0, nullptr, &h);
+        if (rc) {
+            rsos_batch_free(b);
+            return rc;
+        }
+        b->w.jobs.push_back(h);
+        b->w.target.push_back(t_max[i]);
+        b->t_max.push_back(t_max[i]);
+        b->sched.push_back(std::vector<int64_t>{t_max[i]});
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            rsos_batch_free(b);
+            return RSOS_ECUDA;
+        }
+        b->done.push_back(ev);
+        b->reported.push_back(0);
+    }
+    *out = b;
+    return RSOS_OK;
+}
+
+int rsos_batch_schedule(rsos_batch* b, int32_t job, const int64_t* times, int32_t n)
+{
+    if (!b || job < 0 || job >= (int32_t)b->w.jobs.size() || b->queued) return RSOS_EINVAL;
+    if (n < 0 || (n > 0 && !times)) return RSOS_EINVAL;
+    std::vector<int64_t> s(times, times + n);
+    for (size_t k = 0; k < s.size(); ++k) {
+        if (s[k] < 0 || s[k] > b->t_max[job] || (k && s[k] <= s[k - 1])) return RSOS_EINVAL;
+    }
+    if (s.empty() || s.back() != b->t_max[job]) s.push_back(b->t_max[job]);
+    b->sched[job] = s;
+    return RSOS_OK;
+}
+
+int rsos_batch_run(rsos_batch* b, void* stream)
+{
+    if (!b) return RSOS_EINVAL;
+    if (b->queued) return RSOS_EBUSY;
+    cudaStream_t s = as_stream(stream);
+    MultiWork& w = b->w;
+    int rc = RSOS_OK;
+    if (!b->prepared) {
+        w.stops.clear();
+        for (size_t i = 0; i < w.jobs.size(); ++i) {
+            rsos_handle* h = w.jobs[i];
+            rc = rsos_schedule(h, b->sched[i].data(), (int32_t)b->sched[i].size());
+            if (rc) return rc;
+            std::vector<int64_t> st;
+            for (int64_t v : b->sched[i])
+                if (v > h->t) st.push_back(v);
+            if (st.empty() || st.back() != b->t_max[i]) st.push_back(b->t_max[i]);
+            w.stops.push_back(st);
+        }
+        rc = multi_prepare(w);
+        if (rc) return rc;
+        b->prepared = true;
+    }
+    // a measurement due at the start time (t = 0 in the schedule)
+    for (rsos_handle* h : w.jobs) {
+        rc = measure_due(h, s);
+        if (rc) return rc;
+    }
+    const char* env = std::getenv("RSOS_BATCH_GRAPH");
+    const bool use_graph = !(env && std::atoi(env) == 0) && s != nullptr;
+    if (use_graph) {
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            g_init_cuda_err = (int)e;
+            return RSOS_ECUDA;
+        }
+        rc = multi_enqueue(w, s, true, &b->done);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (rc == RSOS_OK && e != cudaSuccess) rc = RSOS_ECUDA;
+        if (rc == RSOS_OK) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (rc == RSOS_OK && e != cudaSuccess) rc = RSOS_ECUDA;
+        b->graph = g;
+        if (rc == RSOS_OK) e = cudaGraphLaunch(b->exec, s);
+        if (rc == RSOS_OK && e != cudaSuccess) rc = RSOS_ECUDA;
+        if (rc != RSOS_OK) {
+            g_init_cuda_err = (int)(e != cudaSuccess ? e : cudaGetLastError());
+            (void)cudaGetLastError();
+        }
+    } else {
+        rc = multi_enqueue(w, s, false, &b->done);
+    }
+    if (rc) {
+        b->status = rc;
+        return rc;
+    }
+    b->queued = true;
+    return RSOS_OK;
+}
+
+int rsos_batch_poll(rsos_batch* b, int32_t* done_ids, int32_t cap, int32_t* n_done)
+{
+    if (!b || !n_done || cap < 0 || (cap > 0 && !done_ids)) return RSOS_EINVAL;
+    *n_done = 0;
+    if (b->status) return b->status;
+    if (!b->queued) return RSOS_EBUSY;
+    bool pending = false;
+    for (size_t i = 0; i < b->w.jobs.size(); ++i) {
+        if (b->reported[i]) continue;
+        const cudaError_t e = cudaEventQuery(b->done[i]);
+        if (e == cudaSuccess) {
+            for (size_t ci = 0; ci < b->w.classes.size(); ++ci)
+                if (b->w.h_err && b->w.h_err[ci]) {
+                    b->status = RSOS_ETIMEOUT;
+                    return RSOS_ETIMEOUT;
+                }
+            if (*n_done < cap) {
+                done_ids[(*n_done)++] = (int32_t)i;
+                b->reported[i] = 1;
+            } else {
+                pending = true;
+            }
+        } else if (e == cudaErrorNotReady) {
+            pending = true;
+        } else {
+            g_init_cuda_err = (int)e;
+            b->status = RSOS_ECUDA;
+            return RSOS_ECUDA;
+        }
+    }
+    return (*n_done == 0 && pending) ? RSOS_EBUSY : RSOS_OK;
+}
+
+int rsos_batch_job(rsos_batch* b, int32_t job, rsos_handle** out)
+{
+    if (!b || !out || job < 0 || job >= (int32_t)b->w.jobs.size()) return RSOS_EINVAL;
+    *out = b->w.jobs[job];
+    return RSOS_OK;
+}
+
+int rsos_batch_free(rsos_batch* b)
+{
+    if (!b) return RSOS_OK;
+    int rc = RSOS_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = RSOS_ECUDA;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
+    multi_release(b->w);
+    for (rsos_handle* h : b->w.jobs) {
+        const int r = rsos_free(h);
+        if (r) rc = r;
+    }
+    delete b;
+    return rc;
+}
 
 }  // extern "C"

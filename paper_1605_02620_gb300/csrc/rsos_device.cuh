@@ -151,7 +151,7 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
 //   sm        block shared-memory base, nthr threads, this thread = tid
 //   wp        lane-word group: words wp*NWT .. wp*NWT+NWT-1
 //   t, p, q   sweep index, phase, active sub-tile set q = perm[p]
-template <int N, typename WT, int SX, bool HAS00, bool CG = false, int NTHR = 0>
+template <int N, typename WT, int SX, bool HAS00, bool CG = false, int NTHR = 0, bool RKEYS = true>
 __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
                                                  int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
                                                  int oy, int k00)
@@ -193,15 +193,20 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
     // blocks of eight are unrolled so every word index is static.
 #pragma unroll 1
     for (int g8 = 0; g8 < (NSEL + 7) / 8; ++g8) {
-        const U4 site_r = philox4x32_10(U4{tile_id, t, (uint32_t)g8, kDomSite | pbits}, J.rk);
+        // RKEYS: round keys from the job descriptor; else derived from the seed
+        // (jobs of a batch read their descriptor from global memory).
+        const U4 site_r = RKEYS ? philox4x32_10(U4{tile_id, t, (uint32_t)g8, kDomSite | pbits}, J.rk)
+                                : philox4x32_10(U4{tile_id, t, (uint32_t)g8, kDomSite | pbits}, J.seed_lo, J.seed_hi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int g = 2 * g8 + h;
             if (NSEL % 8 != 0 && 4 * g >= NSEL) break;
-            const U4 m_lo = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0}, J.rk);
+            const U4 cm = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0};
+            const U4 m_lo = RKEYS ? philox4x32_10(cm, J.rk) : philox4x32_10(cm, J.seed_lo, J.seed_hi);
             U4 m_hi = m_lo;
             if (NWT == 2) {
-                m_hi = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)}, J.rk);
+                const U4 ch = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)};
+                m_hi = RKEYS ? philox4x32_10(ch, J.rk) : philox4x32_10(ch, J.seed_lo, J.seed_hi);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {

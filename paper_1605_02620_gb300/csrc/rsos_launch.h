@@ -38,6 +38,21 @@ struct PersistPlan {
 cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out);
 cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A,
                            const PersistPlan& P, cudaStream_t s);
+// Multi-job launch: all jobs share N, word width and SX.  grid from
+// plan_multi (resident blocks of persistent_multi_kernel).
+cudaError_t plan_multi(int N, int SX, int words_per_thread, int* grid, int* block, size_t* smem);
+cudaError_t launch_multi(int N, int SX, int words_per_thread, const MultiArgs& M, int grid, int block, size_t smem,
+                         cudaStream_t s);
+#define RSOS_DECLARE_MULTI(SX)                                                                        \
+    cudaError_t plan_multi_s##SX(int N, int words_per_thread, int* grid, int* block, size_t* smem);   \
+    cudaError_t launch_multi_s##SX(int N, int words_per_thread, const MultiArgs& M, int grid, int block, \
+                                   size_t smem, cudaStream_t s);
+RSOS_DECLARE_MULTI(1)
+RSOS_DECLARE_MULTI(2)
+RSOS_DECLARE_MULTI(4)
+RSOS_DECLARE_MULTI(8)
+#undef RSOS_DECLARE_MULTI
+
 #define RSOS_DECLARE_PERSIST(SX)                                                                      \
     cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles,             \
                                    PersistPlan* out);                                                  \

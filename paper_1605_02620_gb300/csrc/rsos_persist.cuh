@@ -35,6 +35,7 @@ template <int N, typename WT, int SX>
 struct PersistCfg {
     static constexpr int WPB = persist_warps_per_block(SX, bits_for_step(N), (int)sizeof(WT));
     static constexpr int BLOCK = 32 * WPB;
+    static constexpr int MIN_BLOCKS = 12 / WPB;  // caps registers at ~170 per thread
 };
 
 constexpr long long kWaitIterLimit = 1ll << 26;
@@ -51,6 +52,32 @@ struct PersistArgs {
     int CW;                       // tiles per chunk = TPL * (32 / NWP)
     int TPL;                      // tiles per lane and item
     long long budget_ns;          // time budget of every single wait
+};
+
+// One job of a multi-job (batch) launch: the fields of PersistArgs that
+// differ between jobs.  All jobs of one launch share N, word width and tile
+// edge (one kernel instantiation).
+struct MultiJob {
+    JobDev J;
+    SchedGeom G;
+    const uint32_t* table;
+    unsigned long long* done;
+    unsigned long long* ticket;    // tickets handed out (zeroed before each launch)
+    unsigned long long* finished;  // items completed (zeroed before each launch)
+    unsigned long long n_tickets;  // < 2^31
+    unsigned long long cap;        // most tickets in flight at once
+    uint32_t t0;
+    int CW, TPL;
+    int pad_;
+};
+
+struct MultiArgs {
+    const MultiJob* jobs;
+    int n_jobs;
+    unsigned int* first;      // lowest job index that may still have tickets (zeroed before each launch)
+    unsigned int* exhausted;  // per job: 1 once its tickets ran out (zeroed before each launch)
+    unsigned int* err;
+    long long budget_ns;
 };
 
 #if defined(__CUDACC__)
@@ -99,7 +126,7 @@ static __device__ __noinline__ bool wait_at_least(const unsigned long long* p, u
 // CW = TPL * 32 / NWP consecutive tiles: every lane runs TPL activations in
 // turn, reusing its private window area of the warp's shared memory.
 template <int N, typename WT, int SX>
-__global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK)
+__global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT, SX>::MIN_BLOCKS)
     persistent_kernel(PersistArgs A)
 {
     constexpr int B = bits_for_step(N);
@@ -148,6 +175,122 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK)
         __threadfence();  // the warp's lattice stores, visible GPU-wide before the release
         __syncwarp();
         if (lane == 0) atomicAdd(A.done + (size_t)it.p * A.G.nT + it.r, 1ull);
+    }
+}
+
+// Lane 0: the next (job, ticket).  Jobs are scanned in table order from the
+// lowest one not yet exhausted; a job hands out a ticket only while fewer than
+// its cap are in flight (cap ~ the tickets between an item and its
+// dependencies), so the warps crowd onto as few jobs as keep them busy: large
+// jobs run almost alone with their rows in L2, small ones run many at a time.
+// When every open job is at its cap the scan takes from the first open job.
+static __device__ bool take_multi_ticket(const MultiArgs& M, int* job, unsigned long long* tk)
+{
+    for (int pass = 0; pass < 2; ++pass) {
+        unsigned int j = *(volatile unsigned int*)M.first;
+        for (; j < (unsigned int)M.n_jobs; ++j) {
+            if (*(volatile unsigned int*)&M.exhausted[j]) {
+                if (j == *(volatile unsigned int*)M.first) atomicMax(M.first, j + 1);
+                continue;
+            }
+            const MultiJob& mj = M.jobs[j];
+            if (pass == 0) {
+                const unsigned long long issued = *(volatile unsigned long long*)mj.ticket;
+                const unsigned long long fin = *(volatile unsigned long long*)mj.finished;
+                if (issued >= mj.n_tickets) {
+                    atomicExch(&M.exhausted[j], 1u);
+                    continue;
+                }
+                if (issued - fin >= mj.cap) continue;
+            }
+            const unsigned long long t = atomicAdd(mj.ticket, 1ull);
+            if (t < mj.n_tickets) {
+                *job = (int)j;
+                *tk = t;
+                return true;
+            }
+            atomicExch(&M.exhausted[j], 1u);
+        }
+    }
+    return false;
+}
+
+// Multi-job persistent engine: the single-job worker loop, with each ticket
+// drawn from a job chosen round-robin among the jobs of the launch.  Jobs are
+// independent, so the per-job ticket orders and completion counters keep every
+// argument of the single-job engine (no deadlock, bit-identical results).
+template <int N, typename WT, int SX>
+__global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT, SX>::MIN_BLOCKS)
+    persistent_multi_kernel(MultiArgs M)
+{
+    constexpr int B = bits_for_step(N);
+    constexpr int T = 2 * SX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * (SX + 2) * (SX + 2) * B * 32;
+    int next_job = 0;
+    unsigned long long next_tk = 0;
+    int have = 0;
+    if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
+    for (;;) {
+        int ok = __shfl_sync(0xffffffffu, have, 0);
+        if (lane == 0 && ok) ok = load_relaxed_u32(M.err) == 0u;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const int j = __shfl_sync(0xffffffffu, next_job, 0);
+        const unsigned long long tk = __shfl_sync(0xffffffffu, next_tk, 0);
+        const MultiJob& mj = M.jobs[j];
+        JobDev J;
+        J.planes = mj.J.planes;
+        J.heights = nullptr;
+        J.h00 = mj.J.h00;
+        J.L = mj.J.L;
+        J.T = T;
+        J.nT = mj.J.nT;
+        J.NW = mj.J.NW;
+        J.NWP = mj.J.NWP;
+        J.N = N;
+        J.B = B;
+        J.phase_order = mj.J.phase_order;
+        J.seed_lo = mj.J.seed_lo;
+        J.seed_hi = mj.J.seed_hi;
+        const SchedGeom G = mj.G;
+        const int CW = mj.CW, TPL = mj.TPL;
+        const Item it = item_of_ticket<T>(G, mj.table, tk, mj.t0);
+        Dep d[4];
+        const int nd = item_deps<T>(G, it, d);
+        int waited = 1;
+        if (lane < nd) {
+            waited = wait_at_least(mj.done + (size_t)d[lane].p * G.nT + d[lane].r, d[lane].target, M.err,
+                                   M.budget_ns);
+            if (!waited) atomicCAS(M.err, 0u, kPersistTimeout);
+        }
+        if (!__all_sync(0xffffffffu, waited)) break;
+        if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
+        const int NWP = J.NWP;
+        const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
+        const Control ctl = sweep_control(J.seed_lo, J.seed_hi, it.t, T, T, J.phase_order);
+        const int q = ctl.perm[it.p];
+        const Origin00 o = locate_origin_site_t<T>(J.L, ctl.ox, ctl.oy);
+        if (lane < (32 / NWP) * NWP) {
+            for (int k = 0; k < TPL; ++k) {
+                const int tx = it.c * CW + k * (32 / NWP) + lane_tile;
+                if (tx >= J.nT) break;
+                if (q == o.q && tx == o.tx && it.r == o.ty) {
+                    activate_subtile<N, WT, SX, true, true, 32, false>(J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q,
+                                                                       ctl.ox, ctl.oy, o.k);
+                } else {
+                    activate_subtile<N, WT, SX, false, true, 32, false>(J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p,
+                                                                        q, ctl.ox, ctl.oy, -1);
+                }
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            atomicAdd(mj.done + (size_t)it.p * G.nT + it.r, 1ull);
+            atomicAdd(mj.finished, 1ull);
+        }
     }
 }
 

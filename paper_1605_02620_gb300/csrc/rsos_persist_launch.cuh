@@ -59,6 +59,36 @@ cudaError_t launch_persist_t(const PersistArgs& A, const PersistPlan& P, cudaStr
                                        P.smem, s);
 }
 
+template <int N, typename WT, int SX>
+cudaError_t plan_multi_t(int* grid, int* block, size_t* smem)
+{
+    constexpr int B = bits_for_step(N);
+    constexpr int WPB = PersistCfg<N, WT, SX>::WPB;
+    *block = 32 * WPB;
+    *smem = (size_t)(SX + 2) * (SX + 2) * B * sizeof(WT) * (size_t)(*block);
+    cudaError_t e = cudaFuncSetAttribute(persistent_multi_kernel<N, WT, SX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_multi_kernel<N, WT, SX>, *block, *smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *grid = per_sm * sms;
+    return cudaSuccess;
+}
+
+template <int N, typename WT, int SX>
+cudaError_t launch_multi_t(const MultiArgs& M, int grid, int block, size_t smem, cudaStream_t s)
+{
+    MultiArgs a = M;
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void*)persistent_multi_kernel<N, WT, SX>, dim3(grid), dim3(block), args,
+                                       smem, s);
+}
+
 #define RSOS_PERSIST_SWITCH(CALL_U64, CALL_U32)                                                       \
     switch (J.N) {                                                                                     \
         case 1: return words_per_thread == 2 ? CALL_U64(1) : CALL_U32(1);                              \
@@ -92,6 +122,39 @@ cudaError_t launch_persist_sx(const JobDev& J, int words_per_thread, const Persi
 #undef RSOS_L32
 }
 
+#define RSOS_MULTI_SWITCH(CALL_U64, CALL_U32)                                                         \
+    switch (N) {                                                                                       \
+        case 1: return words_per_thread == 2 ? CALL_U64(1) : CALL_U32(1);                              \
+        case 2: return words_per_thread == 2 ? CALL_U64(2) : CALL_U32(2);                              \
+        case 3: return words_per_thread == 2 ? CALL_U64(3) : CALL_U32(3);                              \
+        case 4: return words_per_thread == 2 ? CALL_U64(4) : CALL_U32(4);                              \
+        case 5: return words_per_thread == 2 ? CALL_U64(5) : CALL_U32(5);                              \
+        case 6: return words_per_thread == 2 ? CALL_U64(6) : CALL_U32(6);                              \
+        case 7: return words_per_thread == 2 ? CALL_U64(7) : CALL_U32(7);                              \
+        default: return cudaErrorInvalidValue;                                                         \
+    }
+
+template <int SX>
+cudaError_t plan_multi_sx(int N, int words_per_thread, int* grid, int* block, size_t* smem)
+{
+#define RSOS_M64(NN) plan_multi_t<NN, uint64_t, SX>(grid, block, smem)
+#define RSOS_M32(NN) plan_multi_t<NN, uint32_t, SX>(grid, block, smem)
+    RSOS_MULTI_SWITCH(RSOS_M64, RSOS_M32)
+#undef RSOS_M64
+#undef RSOS_M32
+}
+
+template <int SX>
+cudaError_t launch_multi_sx(int N, int words_per_thread, const MultiArgs& M, int grid, int block, size_t smem,
+                            cudaStream_t s)
+{
+#define RSOS_L64(NN) launch_multi_t<NN, uint64_t, SX>(M, grid, block, smem, s)
+#define RSOS_L32(NN) launch_multi_t<NN, uint32_t, SX>(M, grid, block, smem, s)
+    RSOS_MULTI_SWITCH(RSOS_L64, RSOS_L32)
+#undef RSOS_L64
+#undef RSOS_L32
+}
+
 }  // namespace rsos
 
 #define RSOS_DEFINE_PERSIST(SX)                                                                       \
@@ -105,5 +168,14 @@ cudaError_t launch_persist_sx(const JobDev& J, int words_per_thread, const Persi
                                      const PersistPlan& P, cudaStream_t s)                            \
     {                                                                                                 \
         return launch_persist_sx<SX>(J, words_per_thread, A, P, s);                                   \
+    }                                                                                                 \
+    cudaError_t plan_multi_s##SX(int N, int words_per_thread, int* grid, int* block, size_t* smem)    \
+    {                                                                                                 \
+        return plan_multi_sx<SX>(N, words_per_thread, grid, block, smem);                             \
+    }                                                                                                 \
+    cudaError_t launch_multi_s##SX(int N, int words_per_thread, const MultiArgs& M, int grid, int block, \
+                                   size_t smem, cudaStream_t s)                                       \
+    {                                                                                                 \
+        return launch_multi_sx<SX>(N, words_per_thread, M, grid, block, smem, s);                     \
     }                                                                                                 \
     }
