@@ -41,7 +41,6 @@ struct rsos_handle {
     // persistent engine
     bool persist;
     rsos::PersistPlan plan;
-    uint32_t* table;
     unsigned long long* done;
     unsigned long long* ticket;
     unsigned int* err;
@@ -154,7 +153,7 @@ Layout layout_of(const rsos_params* p)
         (void)SX;
         l.CW = persist_block_tiles(l.NW / NWT);
         l.K = (nT + l.CW - 1) / l.CW;
-        l.persist = align256((size_t)4 * nT * 8) + align256((size_t)4 * nT * l.K * 4) + 256;
+        l.persist = align256((size_t)4 * nT * 8) + 256;
     }
     l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec + l.persist;
     return l;
@@ -240,7 +239,6 @@ rsos::PersistArgs persist_args(const rsos_handle* h, uint32_t t0, int64_t n)
     A.G.phase_order = h->p.phase_order;
     A.G.seed_lo = h->J.seed_lo;
     A.G.seed_hi = h->J.seed_hi;
-    A.table = h->table;
     A.done = h->done;
     A.ticket = h->ticket;
     A.err = h->err;
@@ -449,7 +447,6 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->rec = reinterpret_cast<int64_t*>(cur);
     cur += l.rec;
     h->persist = l.persist_on;
-    h->table = nullptr;
     h->done = nullptr;
     h->ticket = nullptr;
     h->err = nullptr;
@@ -458,8 +455,6 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
         const int nT = params->L / l.T;
         h->done = reinterpret_cast<unsigned long long*>(cur);
         cur += align256((size_t)4 * nT * 8);
-        h->table = reinterpret_cast<uint32_t*>(cur);
-        cur += align256((size_t)4 * nT * l.K * 4);
         h->ticket = reinterpret_cast<unsigned long long*>(cur);
         h->err = reinterpret_cast<unsigned int*>(cur + 8);
     }
@@ -478,12 +473,6 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     if (l.persist_on) {
         e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, &h->plan);
         if (e == cudaSuccess && (h->plan.CW != l.CW || h->plan.K != l.K)) e = cudaErrorInvalidConfiguration;
-        if (e == cudaSuccess) {
-            std::vector<uint32_t> table((size_t)4 * J.nT * l.K);
-            rsos::build_order_table(J.nT, l.K, h->plan.D, table.data());
-            e = cudaMemcpyAsync(h->table, table.data(), table.size() * 4, cudaMemcpyHostToDevice, as_stream(stream));
-            if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
-        }
         if (e == cudaSuccess) e = rsos::launch_zero(h->done, (size_t)4 * J.nT * 8, as_stream(stream));
         if (e == cudaSuccess) e = rsos::launch_zero(h->ticket, 16, as_stream(stream));
     }
@@ -842,7 +831,6 @@ int multi_enqueue(MultiWork& w, cudaStream_t s, bool capturing, const std::vecto
                 rsos::MultiJob& mj = row[m];
                 mj.J = a.J;
                 mj.G = a.G;
-                mj.table = a.table;
                 mj.done = a.done;
                 mj.ticket = c.d_tickets + m;
                 mj.finished = c.d_tickets + c.members.size() + m;

@@ -3,16 +3,20 @@
 //
 // Data layout in HBM (multisurface path).  A job of S surfaces has
 // NW = ceil(S/32) lane words; bit j of word w is surface 32*w + j.  The
-// residue h mod 2^B of every site is stored in B bit planes.  Within a plane
-// the sites are ordered  [y][x mod T][x div T][w]  ("class-interleaved" by the
-// tile edge T): the same column class of consecutive tiles is contiguous, so a
-// warp whose threads work on consecutive tiles reads and writes one contiguous
-// run of words whatever the random tiling origin of the sweep is.
+// residue h mod 2^B of every site is stored in B bit planes.  Sites are
+// ordered  [y][x mod T][x div T]  ("class-interleaved" by the tile edge T):
+// the same column class of consecutive tiles is contiguous, so a warp whose
+// threads work on consecutive tiles reads and writes one contiguous run
+// whatever the random tiling origin of the sweep is.  Each site is one
+// record of B planes x NW words (plane-major inside the record): for 64
+// surfaces and N = 1 a record is 16 bytes, so one 16-byte copy moves a
+// site and every record starts on a 16-byte boundary.
 //
 // Shared memory (per thread, private): the active sub-tile plus its one-site
-// halo, (SX+2) x (SY+2) slots (corners unused), each slot B words of the
-// thread's lane-word group, stored [slot][plane][thread] so that every thread
-// owns its own bank column: random per-thread site choices never conflict.
+// halo, (SX+2) x (SY+2) slots (corners unused), each slot one record of the
+// thread's lane-word group, stored [slot][thread][plane]: consecutive
+// threads own consecutive records, so random per-thread site choices never
+// conflict and a record is one vector access.
 #pragma once
 #include "philox.cuh"
 #include "rsos_logic.cuh"
@@ -20,7 +24,7 @@
 namespace rsos {
 
 struct JobDev {
-    uint32_t* planes;   // multisurface: B planes of L*L*NW words
+    uint32_t* planes;   // multisurface: L*L site records of B planes x NW words
     int32_t* heights;   // plain path: L*L int32, row-major
     int64_t* h00;       // absolute height of site (0,0) per lane (NW*32)
     int32_t L, T, nT;   // lattice edge, tile edge (square tiles), tiles per row
@@ -59,6 +63,18 @@ RSOS_HD Origin00 locate_origin_site_t(int L, int ox, int oy)
     return locate_origin_site(L, T, ox, oy);
 }
 
+// Index of the record of site (x, y).
+RSOS_HD size_t site_record(const JobDev& J, int x, int y)
+{
+    return ((size_t)y * J.T + (size_t)(x % J.T)) * J.nT + (size_t)(x / J.T);
+}
+
+// Word offset of plane b, lane word w of record rec.
+RSOS_HD size_t plane_word(const JobDev& J, size_t rec, int b, int w)
+{
+    return (rec * (size_t)J.B + (size_t)b) * (size_t)J.NW + (size_t)w;
+}
+
 #if defined(__CUDACC__)
 
 template <typename WT>
@@ -95,21 +111,105 @@ __device__ __forceinline__ void record_origin_deposits(int64_t* h00, int lane_ba
     }
 }
 
-// Global loads of lattice words.  CG = true bypasses L1 (ld.global.cg): in the
-// persistent engine another block may have rewritten the line since this SM
-// last cached it.
-template <typename WT, bool CG>
+// Plain global load of one lattice word (phase-by-phase engine: every phase is
+// its own launch, so no other block writes the lattice meanwhile).
+template <typename WT>
 __device__ __forceinline__ WT load_word(const uint32_t* p)
 {
-    if (CG) {
-        if (sizeof(WT) == 8) return (WT)__ldcg(reinterpret_cast<const unsigned long long*>(p));
-        return (WT)__ldcg(reinterpret_cast<const unsigned int*>(p));
-    }
     return *reinterpret_cast<const WT*>(p);
 }
 
-// Word offsets of the window columns i = -1..SX and rows j = -1..SY of the
-// active sub-tile of tile (tx, ty) in the sweep's tiling.
+// Asynchronous copy of this thread's part of one site record into its
+// shared-memory slot (global -> shared without a register round trip, so all
+// copies of a window are in flight at once).  When the thread owns whole
+// records of a size that is a multiple of 16 bytes (64 surfaces, N = 1: 16 B)
+// they move as 16-byte copies that bypass L1; otherwise plane by plane
+// through L1, which the persistent engines keep coherent by the acquire load
+// they take before every item.
+//   dst   slot in shared memory (B words of WT)
+//   src   plane-0 word of the thread's lane-word group in the record
+template <typename WT, int B>
+__device__ __forceinline__ void stage_record_async(WT* dst, const uint32_t* src, int NW, bool whole_record)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    constexpr int bytes = B * (int)sizeof(WT);
+    if (bytes % 16 == 0 && whole_record) {
+#pragma unroll
+        for (int c = 0; c < bytes / 16; ++c)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * c), "l"(src + 4 * c) : "memory");
+        return;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (sizeof(WT) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8 * b), "l"(src + (size_t)b * NW)
+                         : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4 * b), "l"(src + (size_t)b * NW)
+                         : "memory");
+    }
+}
+
+// Wait for this thread's outstanding asynchronous copies.
+__device__ __forceinline__ void stage_wait_all()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// One record (B words) of a shared-memory slot, as vector accesses where the
+// size allows (16-byte aligned: slots are B * sizeof(WT) bytes apart).
+template <int B, typename WT>
+__device__ __forceinline__ void load_rec(const WT* p, WT (&v)[B])
+{
+    if (B * sizeof(WT) == 16) {
+        if (sizeof(WT) == 8) {
+            const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(p);
+            v[0] = (WT)q.x;
+            v[B - 1] = (WT)q.y;
+        } else {
+            const uint4 q = *reinterpret_cast<const uint4*>(p);
+            v[0] = (WT)q.x;
+            v[1 % B] = (WT)q.y;
+            v[2 % B] = (WT)q.z;
+            v[B - 1] = (WT)q.w;
+        }
+    } else if (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
+        const ulonglong2 q0 = *reinterpret_cast<const ulonglong2*>(p);
+        const ulonglong2 q1 = *reinterpret_cast<const ulonglong2*>(p + 2);
+        v[0] = (WT)q0.x;
+        v[1 % B] = (WT)q0.y;
+        v[2 % B] = (WT)q1.x;
+        v[B - 1] = (WT)q1.y;
+    } else {
+#pragma unroll
+        for (int b = 0; b < B; ++b) v[b] = p[b];
+    }
+}
+
+template <int B, typename WT>
+__device__ __forceinline__ void store_rec(WT* p, const WT (&v)[B])
+{
+    if (B * sizeof(WT) == 16) {
+        if (sizeof(WT) == 8) {
+            *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
+        } else {
+            *reinterpret_cast<uint4*>(p) =
+                make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
+        }
+    } else if (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[1 % B]);
+        *reinterpret_cast<ulonglong2*>(p + 2) =
+            make_ulonglong2((unsigned long long)v[2 % B], (unsigned long long)v[B - 1]);
+    } else {
+#pragma unroll
+        for (int b = 0; b < B; ++b) p[b] = v[b];
+    }
+}
+
+// Word offsets (plane 0, lane word w0) of the window columns i = -1..SX and
+// rows j = -1..SY of the active sub-tile of tile (tx, ty) in the sweep's
+// tiling; plane b is b * NW words further.
 template <int SX>
 struct WindowIndex {
     size_t col[SX + 2];
@@ -122,6 +222,7 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
 {
     constexpr int T = 2 * SX;  // square tiles: the tile edge is known at compile time
     const int nT = J.nT, L = J.L;
+    const size_t rec_words = (size_t)J.B * J.NW;
 #pragma unroll
     for (int ii = 0; ii < SX + 2; ++ii) {
         int xr = ox + qx * SX + ii - 1;  // in [-1, 2T)
@@ -135,13 +236,13 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
         }
         int col = tx + dm;
         col = col < 0 ? col + nT : (col >= nT ? col - nT : col);
-        wi.col[ii] = ((size_t)xr * nT + col) * J.NW + w0;
+        wi.col[ii] = ((size_t)xr * nT + col) * rec_words + w0;
     }
 #pragma unroll
     for (int jj = 0; jj < SX + 2; ++jj) {
         int y = oy + ty * T + qy * SX + jj - 1;  // in [-1, L + T)
         y = y < 0 ? y + L : (y >= L ? y - L : y);
-        wi.row[jj] = (size_t)y * ((size_t)T * nT * J.NW);
+        wi.row[jj] = (size_t)y * ((size_t)T * nT * rec_words);
     }
 }
 
@@ -151,7 +252,9 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
 //   sm        block shared-memory base, nthr threads, this thread = tid
 //   wp        lane-word group: words wp*NWT .. wp*NWT+NWT-1
 //   t, p, q   sweep index, phase, active sub-tile set q = perm[p]
-template <int N, typename WT, int SX, bool HAS00, bool CG = false, int NTHR = 0, bool RKEYS = true>
+// ASYNC = true stages the window with asynchronous copies (persistent
+// engines); otherwise with plain loads through registers.
+template <int N, typename WT, int SX, bool HAS00, bool ASYNC = false, int NTHR = 0, bool RKEYS = true>
 __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
                                                  int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
                                                  int oy, int k00)
@@ -166,7 +269,7 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
     constexpr int NWT = (int)(sizeof(WT) / 4);
     const int qx = q & 1, qy = q >> 1;
     const int w0 = wp * NWT;
-    const size_t plane = (size_t)J.L * J.L * J.NW;
+    const bool whole_record = NWT == J.NW;
 
     WindowIndex<SX> wi;
     window_index<SX>(J, tx, ty, qx, qy, ox, oy, w0, wi);
@@ -179,13 +282,17 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             const bool corner = (jj == 0 || jj == SY + 1) && (ii == 0 || ii == SX + 1);
             if (corner) continue;
             const int s = jj * WW + ii;
+            WT* slot = sm + ((size_t)s * nthr + tid) * B;
+            const uint32_t* src = J.planes + wi.row[jj] + wi.col[ii];
+            if (ASYNC) {
+                stage_record_async<WT, B>(slot, src, J.NW, whole_record);
+            } else {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                const WT v = load_word<WT, CG>(J.planes + b * plane + wi.row[jj] + wi.col[ii]);
-                sm[(size_t)(s * B + b) * nthr + tid] = v;
+                for (int b = 0; b < B; ++b) slot[b] = load_word<WT>(src + (size_t)b * J.NW);
             }
         }
     }
+    if (ASYNC) stage_wait_all();
 
     const uint32_t tile_id = (uint32_t)(ty * J.nT + tx);
     const uint32_t pbits = (uint32_t)p << 28;
@@ -217,20 +324,17 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
                 const uint32_t k = (half * (uint32_t)A) >> 16;
                 const int kx = (int)(k % (uint32_t)SX), ky = (int)(k / (uint32_t)SX);
                 const int s = (ky + 1) * WW + kx + 1;
-                WT* base = sm + (size_t)s * B * nthr + tid;
+                WT* base = sm + ((size_t)s * nthr + tid) * B;
+                const size_t rs = (size_t)nthr * B;  // one slot
                 WT x[B], e[B], w[B], n[B], so[B];
-#pragma unroll
-                for (int b = 0; b < B; ++b) {
-                    x[b] = base[(size_t)b * nthr];
-                    e[b] = base[(size_t)(B + b) * nthr];
-                    w[b] = base[-(ptrdiff_t)(B - b) * nthr];
-                    n[b] = base[-(ptrdiff_t)(WW * B - b) * nthr];
-                    so[b] = base[(size_t)(WW * B + b) * nthr];
-                }
+                load_rec<B, WT>(base, x);
+                load_rec<B, WT>(base + rs, e);
+                load_rec<B, WT>(base - rs, w);
+                load_rec<B, WT>(base - WW * rs, n);
+                load_rec<B, WT>(base + WW * rs, so);
                 const WT acc = accept_mask<N, B, WT>(mask_word<WT>(m_lo, m_hi, r), x, e, w, n, so);
                 masked_increment<B, WT>(x, acc);
-#pragma unroll
-                for (int b = 0; b < B; ++b) base[(size_t)b * nthr] = x[b];
+                store_rec<B, WT>(base, x);
                 if (HAS00 && (int)k == k00) record_origin_deposits<WT>(J.h00, w0 * 32, acc);
             }
         }
@@ -243,10 +347,20 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
 #pragma unroll
         for (int ii = 1; ii <= SX; ++ii) {
             const int s = jj * WW + ii;
+            const WT* slot = sm + ((size_t)s * nthr + tid) * B;
+            uint32_t* dst = J.planes + wi.row[jj] + wi.col[ii];
+            if (B * sizeof(WT) == 16 && whole_record) {
+                WT v[B];
+                load_rec<B, WT>(slot, v);
+                if (sizeof(WT) == 8)
+                    *reinterpret_cast<ulonglong2*>(dst) =
+                        make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
+                else
+                    *reinterpret_cast<uint4*>(dst) =
+                        make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
+            } else {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                *reinterpret_cast<WT*>(J.planes + b * plane + wi.row[jj] + wi.col[ii]) =
-                    sm[(size_t)(s * B + b) * nthr + tid];
+                for (int b = 0; b < B; ++b) *reinterpret_cast<WT*>(dst + (size_t)b * J.NW) = slot[b];
             }
         }
     }

@@ -18,17 +18,11 @@
 
 namespace rsos {
 
-__device__ __forceinline__ size_t site_word(const JobDev& J, int x, int y, int w)
-{
-    return (((size_t)y * J.T + (size_t)(x % J.T)) * J.nT + (size_t)(x / J.T)) * J.NW + w;
-}
-
 __device__ __forceinline__ int lane_residue(const JobDev& J, int x, int y, int w, int lane)
 {
-    const size_t idx = site_word(J, x, y, w);
-    const size_t plane = (size_t)J.L * J.L * J.NW;
+    const size_t rec = site_record(J, x, y);
     int v = 0;
-    for (int b = 0; b < J.B; ++b) v |= (int)((J.planes[b * plane + idx] >> lane) & 1u) << b;
+    for (int b = 0; b < J.B; ++b) v |= (int)((J.planes[plane_word(J, rec, b, w)] >> lane) & 1u) << b;
     return v;
 }
 
@@ -49,14 +43,13 @@ __global__ void __launch_bounds__(1024) row0_prefix_kernel(JobDev J, int32_t* __
     __shared__ int32_t chunk_sum[32][33];
     const int w = blockIdx.x, lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const int L = J.L, B = J.B;
-    const size_t plane = (size_t)L * L * J.NW;
     int32_t* out = row0 + (size_t)(w * 32 + lane) * L;
     int carry = 0;
     for (int X0 = 0; X0 < L; X0 += 1024) {
         __syncthreads();
         for (int k = threadIdx.x; k < 1025; k += blockDim.x) {
             const int x = X0 + k;
-            for (int b = 0; b < B; ++b) words[b][k] = x < L ? J.planes[b * plane + site_word(J, x, 0, w)] : 0u;
+            for (int b = 0; b < B; ++b) words[b][k] = x < L ? J.planes[plane_word(J, site_record(J, x, 0), b, w)] : 0u;
         }
         __syncthreads();
         const int i0 = 32 * c;
@@ -126,11 +119,10 @@ __global__ void __launch_bounds__(256) column_walk_kernel(JobDev J, const int32_
         vprev[k] = 0;
     }
     if (valid && y0 < y1) {
-        const size_t plane = (size_t)L * L * J.NW;
-        const size_t row_stride = (size_t)T * nT * J.NW;
-        size_t idx = site_word(J, x, y0, w);
+        const size_t row_stride = (size_t)T * nT * B * J.NW;  // words per lattice row
+        size_t idx = plane_word(J, site_record(J, x, y0), 0, w);
         uint32_t wv[4] = {0u, 0u, 0u, 0u};
-        for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
+        for (int b = 0; b < B; ++b) wv[b] = J.planes[idx + (size_t)b * J.NW] >> (lg * 8);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             int v = 0;
@@ -141,7 +133,7 @@ __global__ void __launch_bounds__(256) column_walk_kernel(JobDev J, const int32_
         const int ylast = y1 < L ? y1 : L - 1;
         for (int y = y0 + 1; y <= ylast; ++y) {
             idx += row_stride;
-            for (int b = 0; b < B; ++b) wv[b] = J.planes[b * plane + idx] >> (lg * 8);
+            for (int b = 0; b < B; ++b) wv[b] = J.planes[idx + (size_t)b * J.NW] >> (lg * 8);
             const bool inside = y < y1;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {

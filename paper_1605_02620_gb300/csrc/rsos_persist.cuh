@@ -43,7 +43,6 @@ constexpr long long kWaitIterLimit = 1ll << 26;
 struct PersistArgs {
     JobDev J;
     SchedGeom G;
-    const uint32_t* table;        // order table, 4 * nT * K entries
     unsigned long long* done;     // [4][nT] completion counters (cumulative over sweeps)
     unsigned long long* ticket;   // next ticket (zeroed before each launch)
     unsigned int* err;            // error word (0 = ok)
@@ -60,7 +59,6 @@ struct PersistArgs {
 struct MultiJob {
     JobDev J;
     SchedGeom G;
-    const uint32_t* table;
     unsigned long long* done;
     unsigned long long* ticket;    // tickets handed out (zeroed before each launch)
     unsigned long long* finished;  // items completed (zeroed before each launch)
@@ -96,6 +94,18 @@ __device__ __forceinline__ unsigned load_relaxed_u32(const unsigned* p)
     return v;
 }
 
+// Publish the completion of a warp's item: every lane's lattice stores are
+// ordered before the counter increment (warp barrier, then a release fence
+// and a relaxed add by lane 0).
+__device__ __forceinline__ void publish_done(unsigned long long* counter, int lane)
+{
+    __syncwarp();
+    if (lane == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(counter) : "memory");
+    }
+}
+
 __device__ __forceinline__ long long global_ns()
 {
     long long t;
@@ -122,7 +132,9 @@ static __device__ __noinline__ bool wait_at_least(const unsigned long long* p, u
 }
 
 // One worker warp.  Lane 0 owns the ticket stream and fetches the next ticket
-// while the warp works; lanes 0..3 each wait on one dependency.  An item is
+// while the warp works; lanes 0..3 each compute and wait on one dependency.
+// The error word is read only inside waits: a warp that never waits has
+// finitely many items left, and every waiting warp sees the error and stops.  An item is
 // CW = TPL * 32 / NWP consecutive tiles: every lane runs TPL activations in
 // turn, reusing its private window area of the warp's shared memory.
 template <int N, typename WT, int SX>
@@ -141,22 +153,17 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     if (lane == 0) next = atomicAdd(A.ticket, 1ull);
     for (;;) {
         const unsigned long long tk = __shfl_sync(0xffffffffu, next, 0);
-        int ok = tk < A.n_tickets;
-        if (lane == 0 && ok) ok = load_relaxed_u32(A.err) == 0u;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
-        const Item it = item_of_ticket<T>(A.G, A.table, tk, A.t0);
-        Dep d[4];
-        const int nd = item_deps<T>(A.G, it, d);
+        if (tk >= A.n_tickets) break;
+        Control ctl;
+        const Item it = item_of_ticket<T>(A.G, tk, A.t0, &ctl);
+        Dep dep;
         int waited = 1;
-        if (lane < nd) {
-            waited = wait_at_least(A.done + (size_t)d[lane].p * A.G.nT + d[lane].r, d[lane].target, A.err,
-                                   A.budget_ns);
+        if (lane < 4 && item_dep<T>(A.G, it, lane, &dep)) {
+            waited = wait_at_least(A.done + (size_t)dep.p * A.G.nT + dep.r, dep.target, A.err, A.budget_ns);
             if (!waited) atomicCAS(A.err, 0u, kPersistTimeout);
         }
         if (!__all_sync(0xffffffffu, waited)) break;
         if (lane == 0) next = atomicAdd(A.ticket, 1ull);  // overlaps with the work below
-        const Control ctl = sweep_control(A.J.seed_lo, A.J.seed_hi, it.t, T, T, A.J.phase_order);
         const int q = ctl.perm[it.p];
         const Origin00 o = locate_origin_site_t<T>(A.J.L, ctl.ox, ctl.oy);
         if (lane < lanes_used) {
@@ -172,9 +179,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
                 }
             }
         }
-        __threadfence();  // the warp's lattice stores, visible GPU-wide before the release
-        __syncwarp();
-        if (lane == 0) atomicAdd(A.done + (size_t)it.p * A.G.nT + it.r, 1ull);
+        publish_done(A.done + (size_t)it.p * A.G.nT + it.r, lane);
     }
 }
 
@@ -233,10 +238,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     int have = 0;
     if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
     for (;;) {
-        int ok = __shfl_sync(0xffffffffu, have, 0);
-        if (lane == 0 && ok) ok = load_relaxed_u32(M.err) == 0u;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
+        if (!__shfl_sync(0xffffffffu, have, 0)) break;
         const int j = __shfl_sync(0xffffffffu, next_job, 0);
         const unsigned long long tk = __shfl_sync(0xffffffffu, next_tk, 0);
         const MultiJob& mj = M.jobs[j];
@@ -256,20 +258,18 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
         J.seed_hi = mj.J.seed_hi;
         const SchedGeom G = mj.G;
         const int CW = mj.CW, TPL = mj.TPL;
-        const Item it = item_of_ticket<T>(G, mj.table, tk, mj.t0);
-        Dep d[4];
-        const int nd = item_deps<T>(G, it, d);
+        Control ctl;
+        const Item it = item_of_ticket<T>(G, tk, mj.t0, &ctl);
+        Dep dep;
         int waited = 1;
-        if (lane < nd) {
-            waited = wait_at_least(mj.done + (size_t)d[lane].p * G.nT + d[lane].r, d[lane].target, M.err,
-                                   M.budget_ns);
+        if (lane < 4 && item_dep<T>(G, it, lane, &dep)) {
+            waited = wait_at_least(mj.done + (size_t)dep.p * G.nT + dep.r, dep.target, M.err, M.budget_ns);
             if (!waited) atomicCAS(M.err, 0u, kPersistTimeout);
         }
         if (!__all_sync(0xffffffffu, waited)) break;
         if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
         const int NWP = J.NWP;
         const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
-        const Control ctl = sweep_control(J.seed_lo, J.seed_hi, it.t, T, T, J.phase_order);
         const int q = ctl.perm[it.p];
         const Origin00 o = locate_origin_site_t<T>(J.L, ctl.ox, ctl.oy);
         if (lane < (32 / NWP) * NWP) {
@@ -285,12 +285,8 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
                 }
             }
         }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) {
-            atomicAdd(mj.done + (size_t)it.p * G.nT + it.r, 1ull);
-            atomicAdd(mj.finished, 1ull);
-        }
+        publish_done(mj.done + (size_t)it.p * G.nT + it.r, lane);
+        if (lane == 0) atomicAdd(mj.finished, 1ull);
     }
 }
 

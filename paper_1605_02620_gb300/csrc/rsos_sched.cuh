@@ -66,8 +66,22 @@ RSOS_HD int sweep_start_row(const SchedGeom& g, uint32_t t, int oy)
     return wrap1(y - oy, g.L) / T;
 }
 
+// Entries of one sweep's ticket order that lie in slots before s: phase p
+// visits slots D p .. D p + nT - 1 with K chunks each.
+RSOS_HD uint32_t entries_before_slot(const SchedGeom& g, int s)
+{
+    int n = 0;
+    for (int p = 0; p < 4; ++p) {
+        int v = s - g.D * p;
+        v = v < 0 ? 0 : (v > g.nT ? g.nT : v);
+        n += v;
+    }
+    return (uint32_t)n * (uint32_t)g.K;
+}
+
 // Slot-ordered list of (p, j, c) of one sweep: entry = p | j << 2 | c << 20.
-// Host only.  Returns the number of entries (4 * nT * K).
+// Host only: the reference enumeration of the order item_of_ticket computes.
+// Returns the number of entries (4 * nT * K).
 inline int build_order_table(int nT, int K, int D, uint32_t* out)
 {
     int n = 0;
@@ -81,21 +95,43 @@ inline int build_order_table(int nT, int K, int D, uint32_t* out)
     return n;
 }
 
+// Entry e (0 <= e < 4 nT K) of a sweep's ticket order as (p, j, c), the
+// same as build_order_table's, computed without memory traffic: a binary
+// search for the slot holding e, then the phase and chunk among the slot's
+// entries (phases in increasing p, K chunks each).
+RSOS_HD void order_entry(const SchedGeom& g, uint32_t e, int* p, int* j, int* c)
+{
+    const uint32_t K = (uint32_t)g.K;
+    int lo = 0, hi = g.nT + 3 * g.D;  // entries_before_slot(lo) <= e < entries_before_slot(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (entries_before_slot(g, mid) <= e) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t o = e - entries_before_slot(g, lo);
+    int p0 = 0;
+    while (lo - g.D * p0 >= g.nT) ++p0;  // first phase visiting slot lo
+    const uint32_t pi = o / K;
+    *p = p0 + (int)pi;
+    *c = (int)(o - pi * K);
+    *j = lo - g.D * *p;
+}
+
 // Item of a ticket; tickets of one launch are 32-bit (launches are split).
+// Also returns the sweep's control draw (nullable).
 template <int TT = 0>
-RSOS_HD Item item_of_ticket(const SchedGeom& g, const uint32_t* table, uint64_t ticket, uint32_t t0)
+RSOS_HD Item item_of_ticket(const SchedGeom& g, uint64_t ticket, uint32_t t0, Control* ctl_out = nullptr)
 {
     const uint32_t per_sweep = 4u * (uint32_t)g.nT * (uint32_t)g.K;
     const uint32_t tk = (uint32_t)ticket;
     const uint32_t sw = tk / per_sweep;
     Item it;
     it.t = t0 + sw;
-    const uint32_t e = table[tk - sw * per_sweep];
-    it.p = (int)(e & 3u);
-    const int j = (int)((e >> 2) & 0x3FFFFu);
-    it.c = (int)(e >> 20);
+    int j = 0;
+    order_entry(g, tk - sw * per_sweep, &it.p, &j, &it.c);
     const int T = TT > 0 ? TT : g.T;
     const Control ctl = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order);
+    if (ctl_out) *ctl_out = ctl;
     int r = sweep_start_row<TT>(g, it.t, ctl.oy) + it.p + j;  // <= 2 nT + 1
     r = r >= g.nT ? r - g.nT : r;
     r = r >= g.nT ? r - g.nT : r;
@@ -103,41 +139,53 @@ RSOS_HD Item item_of_ticket(const SchedGeom& g, const uint32_t* table, uint64_t 
     return it;
 }
 
-// Dependencies of an item; returns their number (<= 4).
+// Dependency k (0 <= k < 4) of an item, if it has one (at most four: three
+// tile rows, four for T = 2 at a sweep boundary).  Each lane of a worker warp
+// computes its own, in registers.
 template <int TT = 0>
-RSOS_HD int item_deps(const SchedGeom& g, const Item& it, Dep* out)
+RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, Dep* out)
 {
-    int n = 0;
     const int T = TT > 0 ? TT : g.T;
     if (it.p > 0) {
         const uint64_t target = ((uint64_t)it.t + 1) * (uint64_t)g.K;
-        const int lo = g.nT >= 3 ? -1 : 0, hi = g.nT >= 3 ? 1 : g.nT - 1;
-        for (int d = lo; d <= hi; ++d) {
-            const int r = wrap1(it.r + d, g.nT);
-            bool dup = false;
-            for (int k = 0; k < n; ++k) dup |= out[k].r == r;
-            if (!dup) out[n++] = Dep{it.p - 1, r, target};
+        if (g.nT >= 3) {
+            if (k > 2) return false;
+            *out = Dep{it.p - 1, wrap1(it.r + k - 1, g.nT), target};
+        } else {
+            if (k >= g.nT) return false;
+            *out = Dep{it.p - 1, wrap1(it.r + k, g.nT), target};
         }
-        return n;
+        return true;
     }
-    if (it.t == 0) return 0;
+    if (it.t == 0 || k > 3) return false;
     const int oy_now = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order).oy;
     const int oy_prev = sweep_control(g.seed_lo, g.seed_hi, it.t - 1, T, T, g.phase_order).oy;
     // Rows r' of the previous tiling whose first site row oy_prev + r' T lies
     // in (y0 - T - 2, y0 + T + 2), y0 = first site row of this tile row: the
     // offsets y0 + dy, dy in [-(T+1), T+1], that are multiples of T from oy_prev.
-    const uint64_t target = (uint64_t)it.t * (uint64_t)g.K;
     const int base = it.r * T + oy_now - oy_prev;  // y0 - oy_prev, in (-T, L + T)
     // smallest dy >= -(T+1) with base + dy = 0 mod T
-    int dy = -(T + 1);
-    int rem = (base + dy) % T;
+    int dy0 = -(T + 1);
+    int rem = (base + dy0) % T;
     if (rem < 0) rem += T;
-    if (rem) dy += T - rem;
-    for (; dy <= T + 1; dy += T) {
-        const int r = mod_pos((base + dy) / T, g.nT);  // base + dy is a multiple of T
-        bool dup = false;
-        for (int k = 0; k < n; ++k) dup |= out[k].r == r;
-        if (!dup && n < 4) out[n++] = Dep{3, r, target};
+    if (rem) dy0 += T - rem;
+    const int dy = dy0 + k * T;
+    if (dy > T + 1) return false;
+    const int r = mod_pos((base + dy) / T, g.nT);  // base + dy is a multiple of T
+    for (int k2 = 0; k2 < k; ++k2)  // rows already covered by an earlier dependency
+        if (mod_pos((base + dy0 + k2 * T) / T, g.nT) == r) return false;
+    *out = Dep{3, r, (uint64_t)it.t * (uint64_t)g.K};
+    return true;
+}
+
+// All dependencies of an item, packed (host tests).
+template <int TT = 0>
+RSOS_HD int item_deps(const SchedGeom& g, const Item& it, Dep* out)
+{
+    int n = 0;
+    for (int k = 0; k < 4; ++k) {
+        Dep d;
+        if (item_dep<TT>(g, it, k, &d)) out[n++] = d;
     }
     return n;
 }

@@ -88,9 +88,16 @@ static rsos::SchedGeom make_geom(const int* g8)
 
 int probe_order_table(int nT, int K, int D, uint32_t* out) { return rsos::build_order_table(nT, K, D, out); }
 
-void probe_item(const int* g8, const uint32_t* table, uint64_t ticket, uint32_t t0, int* out4)
+void probe_order_entry(int nT, int K, int D, uint32_t e, int* out3)
 {
-    const rsos::Item it = rsos::item_of_ticket<0>(make_geom(g8), table, ticket, t0);
+    rsos::SchedGeom g{};
+    g.nT = nT; g.K = K; g.D = D;
+    rsos::order_entry(g, e, &out3[0], &out3[1], &out3[2]);
+}
+
+void probe_item(const int* g8, uint64_t ticket, uint32_t t0, int* out4)
+{
+    const rsos::Item it = rsos::item_of_ticket<0>(make_geom(g8), ticket, t0);
     out4[0] = (int)it.t; out4[1] = it.p; out4[2] = it.r; out4[3] = it.c;
 }
 

@@ -33,9 +33,28 @@ def probe(tmp_path_factory):
     ip = ctypes.POINTER(ctypes.c_int)
     u32p = ctypes.POINTER(ctypes.c_uint32)
     lib.probe_order_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p]
-    lib.probe_item.argtypes = [ip, u32p, ctypes.c_uint64, ctypes.c_uint32, ip]
+    lib.probe_order_entry.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ip]
+    lib.probe_item.argtypes = [ip, ctypes.c_uint64, ctypes.c_uint32, ip]
     lib.probe_deps.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_int64)]
     return lib
+
+
+@pytest.mark.parametrize("nT,K,D", [
+    (1, 1, 2), (2, 3, 2), (3, 1, 2), (5, 2, 3), (8, 4, 2), (8, 1, 9), (12, 3, 4), (12, 2, 5),
+    (31, 3, 7), (64, 8, 21), (64, 2, 40), (512, 8, 91), (512, 8, 170), (512, 4, 300),
+])
+def test_order_entry_matches_table(probe, nT, K, D):
+    """The device computes a ticket's (phase, visit row, chunk) arithmetically;
+    it must enumerate exactly the slot-ordered table, including phase lags
+    above nT/3 where the phase fronts overlap differently."""
+    table = np.zeros(4 * nT * K, dtype=np.uint32)
+    n = probe.probe_order_table(nT, K, D, table.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    assert n == 4 * nT * K
+    out = np.zeros(3, dtype=np.int32)
+    for e in range(n):
+        probe.probe_order_entry(nT, K, D, e, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        v = int(table[e])
+        assert (int(out[0]), int(out[1]), int(out[2])) == (v & 3, (v >> 2) & 0x3FFFF, v >> 20), e
 
 
 def _footprint(L, T, ox, oy, q, ty, txs):
@@ -74,8 +93,7 @@ def test_schedule_is_sound(probe, L, T, CW, D, seed, order):
     items, ticket_of = [], {}
     out = np.zeros(4, dtype=np.int32)
     for tk in range(n_sweeps * n):
-        probe.probe_item(gp, table.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), tk, 0,
-                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        probe.probe_item(gp, tk, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         it = tuple(int(v) for v in out)
         assert it not in ticket_of
         ticket_of[it] = tk
