@@ -246,55 +246,22 @@ __device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, in
     }
 }
 
-// One activation of one sub-tile for one lane-word group (section II):
-// stage sub-tile + halo into the thread's private shared-memory slots, run the
-// 2a selections in order, write the interior back.
-//   sm        block shared-memory base, nthr threads, this thread = tid
-//   wp        lane-word group: words wp*NWT .. wp*NWT+NWT-1
-//   t, p, q   sweep index, phase, active sub-tile set q = perm[p]
-// ASYNC = true stages the window with asynchronous copies (persistent
-// engines); otherwise with plain loads through registers.
-template <int N, typename WT, int SX, bool HAS00, bool ASYNC = false, int NTHR = 0, bool RKEYS = true>
-__device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
-                                                 int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
-                                                 int oy, int k00)
+// The 2a selections of one sub-tile activation (section II; Eq. 6 per
+// selection) on a window already staged in shared memory: slot s of this
+// thread at sm[((s * nthr) + tid) * B], (SX+2)^2 slots row-major with the
+// sub-tile at rows and columns 1..SX.
+//   tile_id   tile index of the Philox counters;  w0  first lane word
+//   k00       site index of global site (0,0) in this sub-tile (HAS00)
+template <int N, typename WT, int SX, bool HAS00, int NTHR = 0, bool RKEYS = true>
+__device__ __forceinline__ void select_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
+                                               uint32_t tile_id, uint32_t t, int p, int w0, int k00)
 {
-    // A compile-time block size turns every slot offset into an immediate.
     const int nthr = NTHR > 0 ? NTHR : nthr_rt;
     constexpr int B = bits_for_step(N);
-    constexpr int SY = SX;
-    constexpr int A = SX * SY;
+    constexpr int A = SX * SX;
     constexpr int NSEL = 2 * A;
     constexpr int WW = SX + 2;
     constexpr int NWT = (int)(sizeof(WT) / 4);
-    const int qx = q & 1, qy = q >> 1;
-    const int w0 = wp * NWT;
-    const bool whole_record = NWT == J.NW;
-
-    WindowIndex<SX> wi;
-    window_index<SX>(J, tx, ty, qx, qy, ox, oy, w0, wi);
-    constexpr int UNROLL_ROWS = SX <= 4 ? SY + 2 : 1;
-
-#pragma unroll UNROLL_ROWS
-    for (int jj = 0; jj < SY + 2; ++jj) {
-#pragma unroll
-        for (int ii = 0; ii < SX + 2; ++ii) {
-            const bool corner = (jj == 0 || jj == SY + 1) && (ii == 0 || ii == SX + 1);
-            if (corner) continue;
-            const int s = jj * WW + ii;
-            WT* slot = sm + ((size_t)s * nthr + tid) * B;
-            const uint32_t* src = J.planes + wi.row[jj] + wi.col[ii];
-            if (ASYNC) {
-                stage_record_async<WT, B>(slot, src, J.NW, whole_record);
-            } else {
-#pragma unroll
-                for (int b = 0; b < B; ++b) slot[b] = load_word<WT>(src + (size_t)b * J.NW);
-            }
-        }
-    }
-    if (ASYNC) stage_wait_all();
-
-    const uint32_t tile_id = (uint32_t)(ty * J.nT + tx);
     const uint32_t pbits = (uint32_t)p << 28;
     // Eight selections per site draw (16-bit halves), four per mask draw; the
     // blocks of eight are unrolled so every word index is static.
@@ -339,6 +306,56 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             }
         }
     }
+
+}
+
+// One activation of one sub-tile for one lane-word group (section II):
+// stage sub-tile + halo into the thread's private shared-memory slots, run the
+// 2a selections in order, write the interior back.
+//   sm        block shared-memory base, nthr threads, this thread = tid
+//   wp        lane-word group: words wp*NWT .. wp*NWT+NWT-1
+//   t, p, q   sweep index, phase, active sub-tile set q = perm[p]
+// ASYNC = true stages the window with asynchronous copies (persistent
+// engines); otherwise with plain loads through registers.
+template <int N, typename WT, int SX, bool HAS00, bool ASYNC = false, int NTHR = 0, bool RKEYS = true>
+__device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict__ sm, int tid, int nthr_rt,
+                                                 int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
+                                                 int oy, int k00)
+{
+    // A compile-time block size turns every slot offset into an immediate.
+    const int nthr = NTHR > 0 ? NTHR : nthr_rt;
+    constexpr int B = bits_for_step(N);
+    constexpr int SY = SX;
+    constexpr int WW = SX + 2;
+    constexpr int NWT = (int)(sizeof(WT) / 4);
+    const int qx = q & 1, qy = q >> 1;
+    const int w0 = wp * NWT;
+    const bool whole_record = NWT == J.NW;
+
+    WindowIndex<SX> wi;
+    window_index<SX>(J, tx, ty, qx, qy, ox, oy, w0, wi);
+    constexpr int UNROLL_ROWS = SX <= 4 ? SY + 2 : 1;
+
+#pragma unroll UNROLL_ROWS
+    for (int jj = 0; jj < SY + 2; ++jj) {
+#pragma unroll
+        for (int ii = 0; ii < SX + 2; ++ii) {
+            const bool corner = (jj == 0 || jj == SY + 1) && (ii == 0 || ii == SX + 1);
+            if (corner) continue;
+            const int s = jj * WW + ii;
+            WT* slot = sm + ((size_t)s * nthr + tid) * B;
+            const uint32_t* src = J.planes + wi.row[jj] + wi.col[ii];
+            if (ASYNC) {
+                stage_record_async<WT, B>(slot, src, J.NW, whole_record);
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) slot[b] = load_word<WT>(src + (size_t)b * J.NW);
+            }
+        }
+    }
+    if (ASYNC) stage_wait_all();
+
+    select_subtile<N, WT, SX, HAS00, NTHR, RKEYS>(J, sm, tid, nthr, (uint32_t)(ty * J.nT + tx), t, p, w0, k00);
 
     // Recomputed rather than kept live across the selection loop (registers).
     window_index<SX>(J, tx, ty, qx, qy, ox, oy, w0, wi);

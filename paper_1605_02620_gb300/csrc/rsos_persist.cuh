@@ -151,21 +151,25 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     const int lanes_used = (32 / NWP) * NWP;
     unsigned long long next = 0;
     if (lane == 0) next = atomicAdd(A.ticket, 1ull);
+    SweepCtx sc;
+    sc.t = 0xffffffffu;
+    Origin00 o{};
     for (;;) {
         const unsigned long long tk = __shfl_sync(0xffffffffu, next, 0);
         if (tk >= A.n_tickets) break;
-        Control ctl;
-        const Item it = item_of_ticket<T>(A.G, tk, A.t0, &ctl);
+        const uint32_t t_before = sc.t;
+        const Item it = item_of_ticket<T>(A.G, tk, A.t0, &sc);
+        if (sc.t != t_before) o = locate_origin_site_t<T>(A.J.L, sc.ctl.ox, sc.ctl.oy);
+        const Control& ctl = sc.ctl;
         Dep dep;
         int waited = 1;
-        if (lane < 4 && item_dep<T>(A.G, it, lane, &dep)) {
+        if (lane < 4 && item_dep<T>(A.G, it, lane, sc, &dep)) {
             waited = wait_at_least(A.done + (size_t)dep.p * A.G.nT + dep.r, dep.target, A.err, A.budget_ns);
             if (!waited) atomicCAS(A.err, 0u, kPersistTimeout);
         }
         if (!__all_sync(0xffffffffu, waited)) break;
         if (lane == 0) next = atomicAdd(A.ticket, 1ull);  // overlaps with the work below
         const int q = ctl.perm[it.p];
-        const Origin00 o = locate_origin_site_t<T>(A.J.L, ctl.ox, ctl.oy);
         if (lane < lanes_used) {
             for (int k = 0; k < A.TPL; ++k) {
                 const int tx = it.c * A.CW + k * (32 / NWP) + lane_tile;
@@ -236,6 +240,10 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     int next_job = 0;
     unsigned long long next_tk = 0;
     int have = 0;
+    SweepCtx sc;
+    sc.t = 0xffffffffu;
+    int sc_job = -1;
+    Origin00 o{};
     if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
     for (;;) {
         if (!__shfl_sync(0xffffffffu, have, 0)) break;
@@ -258,11 +266,15 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
         J.seed_hi = mj.J.seed_hi;
         const SchedGeom G = mj.G;
         const int CW = mj.CW, TPL = mj.TPL;
-        Control ctl;
-        const Item it = item_of_ticket<T>(G, tk, mj.t0, &ctl);
+        if (j != sc_job) sc.t = 0xffffffffu;  // the cached sweep belongs to another job
+        sc_job = j;
+        const uint32_t t_before = sc.t;
+        const Item it = item_of_ticket<T>(G, tk, mj.t0, &sc);
+        if (sc.t != t_before) o = locate_origin_site_t<T>(J.L, sc.ctl.ox, sc.ctl.oy);
+        const Control& ctl = sc.ctl;
         Dep dep;
         int waited = 1;
-        if (lane < 4 && item_dep<T>(G, it, lane, &dep)) {
+        if (lane < 4 && item_dep<T>(G, it, lane, sc, &dep)) {
             waited = wait_at_least(mj.done + (size_t)dep.p * G.nT + dep.r, dep.target, M.err, M.budget_ns);
             if (!waited) atomicCAS(M.err, 0u, kPersistTimeout);
         }
@@ -271,7 +283,6 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
         const int NWP = J.NWP;
         const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
         const int q = ctl.perm[it.p];
-        const Origin00 o = locate_origin_site_t<T>(J.L, ctl.ox, ctl.oy);
         if (lane < (32 / NWP) * NWP) {
             for (int k = 0; k < TPL; ++k) {
                 const int tx = it.c * CW + k * (32 / NWP) + lane_tile;

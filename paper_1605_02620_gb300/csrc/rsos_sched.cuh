@@ -102,6 +102,33 @@ inline int build_order_table(int nT, int K, int D, uint32_t* out)
 RSOS_HD void order_entry(const SchedGeom& g, uint32_t e, int* p, int* j, int* c)
 {
     const uint32_t K = (uint32_t)g.K;
+    const int D = g.D, nT = g.nT;
+    if (3 * D <= nT) {
+        // The phase fronts enter one after another, all four run together,
+        // then they leave one after another: seven segments of slots with
+        // m = 1, 2, 3, 4, 3, 2, 1 phases (first phase p_lo) and m K entries each.
+        // entries before segment k (in units of K): D * {0, 1, 3, 6} entering,
+        // 4 nT - D * {6, 3, 1} leaving (triangular numbers)
+        auto before = [&](int k) {
+            return k < 4 ? (uint32_t)D * (uint32_t)(k * (k + 1) / 2)
+                         : 4u * (uint32_t)nT - (uint32_t)D * (uint32_t)((7 - k) * (8 - k) / 2);
+        };
+        int seg = 0;
+#pragma unroll
+        for (int k = 1; k < 7; ++k) seg += e >= before(k) * K ? 1 : 0;
+        const int m = seg < 4 ? seg + 1 : 7 - seg;
+        const int p_lo = seg < 4 ? 0 : seg - 3;
+        const int s0 = seg < 4 ? seg * D : nT + (seg - 4) * D;
+        const uint32_t off = e - before(seg) * K;
+        const uint32_t per_slot = (uint32_t)m * K;
+        const uint32_t ds = off / per_slot;
+        const uint32_t o = off - ds * per_slot;
+        const uint32_t pi = o / K;
+        *p = p_lo + (int)pi;
+        *c = (int)(o - pi * K);
+        *j = s0 + (int)ds - D * *p;
+        return;
+    }
     int lo = 0, hi = g.nT + 3 * g.D;  // entries_before_slot(lo) <= e < entries_before_slot(hi)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -117,33 +144,61 @@ RSOS_HD void order_entry(const SchedGeom& g, uint32_t e, int* p, int* j, int* c)
     *j = lo - g.D * *p;
 }
 
-// Item of a ticket; tickets of one launch are 32-bit (launches are split).
-// Also returns the sweep's control draw (nullable).
+// Per-sweep quantities of the items of one sweep, computed once per sweep
+// (a worker's consecutive tickets mostly share one).
+struct SweepCtx {
+    uint32_t t;     // sweep (0xffffffff: none yet)
+    Control ctl;    // its control draw
+    int start_row;  // tile row where its phase 0 starts
+    int oy_prev;    // row offset of the previous sweep's tiling (t > 0)
+};
+
 template <int TT = 0>
-RSOS_HD Item item_of_ticket(const SchedGeom& g, uint64_t ticket, uint32_t t0, Control* ctl_out = nullptr)
+RSOS_HD void sweep_ctx(const SchedGeom& g, uint32_t t, SweepCtx* c)
+{
+    const int T = TT > 0 ? TT : g.T;
+    c->t = t;
+    c->ctl = sweep_control(g.seed_lo, g.seed_hi, t, T, T, g.phase_order);
+    c->start_row = sweep_start_row<TT>(g, t, c->ctl.oy);
+    c->oy_prev = t > 0 ? sweep_control(g.seed_lo, g.seed_hi, t - 1, T, T, g.phase_order).oy : 0;
+}
+
+// Item of a ticket; tickets of one launch are 32-bit (launches are split).
+// c caches the sweep's quantities and is refreshed when the sweep changes.
+template <int TT = 0>
+RSOS_HD Item item_of_ticket(const SchedGeom& g, uint64_t ticket, uint32_t t0, SweepCtx* c)
 {
     const uint32_t per_sweep = 4u * (uint32_t)g.nT * (uint32_t)g.K;
     const uint32_t tk = (uint32_t)ticket;
     const uint32_t sw = tk / per_sweep;
     Item it;
     it.t = t0 + sw;
+    if (c->t != it.t) sweep_ctx<TT>(g, it.t, c);
     int j = 0;
     order_entry(g, tk - sw * per_sweep, &it.p, &j, &it.c);
-    const int T = TT > 0 ? TT : g.T;
-    const Control ctl = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order);
-    if (ctl_out) *ctl_out = ctl;
-    int r = sweep_start_row<TT>(g, it.t, ctl.oy) + it.p + j;  // <= 2 nT + 1
+    int r = c->start_row + it.p + j;  // <= 2 nT + 1
     r = r >= g.nT ? r - g.nT : r;
     r = r >= g.nT ? r - g.nT : r;
     it.r = g.nT >= 2 ? r : 0;
     return it;
 }
 
+// Same, without a cache; returns the sweep's control draw (nullable).
+template <int TT = 0>
+RSOS_HD Item item_of_ticket(const SchedGeom& g, uint64_t ticket, uint32_t t0, Control* ctl_out = nullptr)
+{
+    SweepCtx c;
+    c.t = 0xffffffffu;
+    const Item it = item_of_ticket<TT>(g, ticket, t0, &c);
+    if (ctl_out) *ctl_out = c.ctl;
+    return it;
+}
+
 // Dependency k (0 <= k < 4) of an item, if it has one (at most four: three
 // tile rows, four for T = 2 at a sweep boundary).  Each lane of a worker warp
-// computes its own, in registers.
+// computes its own, in registers.  c: the item's sweep (item_of_ticket).
 template <int TT = 0>
-RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, Dep* out)
+RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, const SweepCtx& c, Dep* out)
 {
     const int T = TT > 0 ? TT : g.T;
     if (it.p > 0) {
@@ -158,12 +213,10 @@ RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, Dep* out)
         return true;
     }
     if (it.t == 0 || k > 3) return false;
-    const int oy_now = sweep_control(g.seed_lo, g.seed_hi, it.t, T, T, g.phase_order).oy;
-    const int oy_prev = sweep_control(g.seed_lo, g.seed_hi, it.t - 1, T, T, g.phase_order).oy;
     // Rows r' of the previous tiling whose first site row oy_prev + r' T lies
     // in (y0 - T - 2, y0 + T + 2), y0 = first site row of this tile row: the
     // offsets y0 + dy, dy in [-(T+1), T+1], that are multiples of T from oy_prev.
-    const int base = it.r * T + oy_now - oy_prev;  // y0 - oy_prev, in (-T, L + T)
+    const int base = it.r * T + c.ctl.oy - c.oy_prev;  // y0 - oy_prev, in (-T, L + T)
     // smallest dy >= -(T+1) with base + dy = 0 mod T
     int dy0 = -(T + 1);
     int rem = (base + dy0) % T;
@@ -171,11 +224,28 @@ RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, Dep* out)
     if (rem) dy0 += T - rem;
     const int dy = dy0 + k * T;
     if (dy > T + 1) return false;
-    const int r = mod_pos((base + dy) / T, g.nT);  // base + dy is a multiple of T
+    // (base + dy) / T is in [-2, nT + 2): exact division, wrapped by additions
+    auto row_of = [&](int d) {
+        int r = (base + d) / T;
+        r = r < 0 ? r + g.nT : r;
+        r = r >= g.nT ? r - g.nT : r;
+        r = r < 0 ? r + g.nT : r;
+        return r >= g.nT ? r - g.nT : r;
+    };
+    const int r = row_of(dy);
     for (int k2 = 0; k2 < k; ++k2)  // rows already covered by an earlier dependency
-        if (mod_pos((base + dy0 + k2 * T) / T, g.nT) == r) return false;
+        if (row_of(dy0 + k2 * T) == r) return false;
     *out = Dep{3, r, (uint64_t)it.t * (uint64_t)g.K};
     return true;
+}
+
+// Same, computing the sweep's quantities itself (host tests).
+template <int TT = 0>
+RSOS_HD bool item_dep(const SchedGeom& g, const Item& it, int k, Dep* out)
+{
+    SweepCtx c;
+    sweep_ctx<TT>(g, it.t, &c);
+    return item_dep<TT>(g, it, k, c, out);
 }
 
 // All dependencies of an item, packed (host tests).
