@@ -32,13 +32,14 @@ cudaError_t plan_persist_t(const JobDev& J, int block_tiles, PersistPlan* P)
     P->grid = per_sm * sms;
     // Phase lag D (slots between consecutive phase fronts).  A dependency sits
     // about D slots (D * 4K tickets) behind its dependant; with two tickets
-    // per worker warp in flight, D = 0.8 * in-flight / (4K) keeps most
-    // dependencies complete by the time they are checked while the 3D tile
-    // rows between the phase-0 and phase-3 fronts still mostly hit L2 (for
-    // L = 4096, N = 1, 64 surfaces: D ~ 96; measured best among 42..128).
+    // per worker warp in flight, D = 1.5 * in-flight / (4K) keeps dependencies
+    // complete by the time they are checked (L = 4096, N = 1, 64 surfaces:
+    // D = nT / 3 = 170; measured flat from 150 to 340, 6% slower at 91, 24%
+    // at 48).  The rows between the fronts need not fit in L2: with 16-byte
+    // site records the re-reads cost less than the waits a short lag causes.
     const int per_slot = 4 * P->K;
     const int workers = P->grid * WPB;
-    int D = (int)(0.8 * 2.0 * workers / per_slot);
+    int D = (int)(1.5 * 2.0 * workers / per_slot);
     const int dmax = J.nT / 3 > 2 ? J.nT / 3 : 2;
     if (D > dmax) D = dmax;
     if (D < 2) D = 2;
