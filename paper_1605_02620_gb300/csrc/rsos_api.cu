@@ -63,15 +63,17 @@ struct Layout {
 };
 
 // Tiles per lane and work item of the persistent engine (execution geometry
-// only; RSOS_TILES_PER_LANE overrides the default of 2, the fastest measured
-// for L = 4096, N = 1, 64 surfaces on GB300).
-int persist_tiles_per_lane()
+// only): by default an item is 64 tiles (2 per lane with one thread per
+// tile, 4 with two), the fastest measured for L = 4096 and 64 surfaces on
+// GB300 at N = 1 and N = 2, and at most 8 per lane for wider jobs;
+// RSOS_TILES_PER_LANE overrides it.
+int persist_tiles_per_lane(int NWP)
 {
     if (const char* env = std::getenv("RSOS_TILES_PER_LANE")) {
         const int v = std::atoi(env);
         if (v >= 1 && v <= 64) return v;
     }
-    return 2;
+    return NWP <= 4 ? 2 * NWP : 8;
 }
 
 // Tiles per work item: one warp's 32 lanes over the lane-word groups of a
@@ -79,19 +81,25 @@ int persist_tiles_per_lane()
 int persist_block_tiles(int NWP)
 {
     const int cw = 32 / NWP;
-    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane();
+    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane(NWP);
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// 32-lane words per thread: 2 when the job has an even number of words
-// (uint64 registers), else 1.  RSOS_WORDS_PER_THREAD=1 forces one word per
-// thread (execution geometry only; results are identical).
-int words_per_thread(int NW)
+// 32-lane words per thread: 2 (uint64 registers) when the job has an even
+// number of words and 2 bit planes, else 1.  With 3 or 4 planes a uint64
+// window is 1.5-2x larger, so fewer warps fit an SM; one word per thread was
+// measured faster there (L = 4096, 64 surfaces: 287 vs 305 us per sweep at
+// N = 2, 420 vs 499 at N = 4), unless it would need more than 32 threads per
+// tile.  RSOS_WORDS_PER_THREAD=1 forces one word per thread (execution
+// geometry only; results are identical).
+int words_per_thread(int NW, int N)
 {
     if (const char* env = std::getenv("RSOS_WORDS_PER_THREAD"))
         if (std::atoi(env) == 1) return 1;
-    return (NW % 2 == 0) ? 2 : 1;
+    if (NW % 2 != 0) return 1;
+    if (rsos::bits_for_step(N) >= 3 && NW <= 32) return 1;
+    return 2;
 }
 
 int validate(const rsos_params* p)
@@ -109,7 +117,7 @@ int validate(const rsos_params* p)
     if (p->engine < 0 || p->engine > 2) return RSOS_EINVAL;
     if (p->engine == 2 && p->surfaces == 1) return RSOS_EINVAL;  // plain path: phase engine only
     if (p->engine == 2) {
-        const int NW = (p->surfaces + 31) / 32, NWT = words_per_thread(NW);
+        const int NW = (p->surfaces + 31) / 32, NWT = words_per_thread(NW, p->N);
         if (NW / NWT > 32) return RSOS_EINVAL;
     }
     return RSOS_OK;
@@ -142,13 +150,13 @@ Layout layout_of(const rsos_params* p)
     l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && nT >= 8));
     if (l.persist_on && p->engine == 0) {
         // more lane-word groups than lanes of a warp: phase engine
-        const int NWT = words_per_thread(l.NW);
+        const int NWT = words_per_thread(l.NW, p->N);
         if (l.NW / NWT > 32) l.persist_on = false;
     }
     l.CW = l.K = 0;
     l.persist = 0;
     if (l.persist_on) {
-        const int NWT = words_per_thread(l.NW);
+        const int NWT = words_per_thread(l.NW, p->N);
         const int SX = l.T / 2;
         (void)SX;
         l.CW = persist_block_tiles(l.NW / NWT);
@@ -403,7 +411,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->SX = l.T / 2;
     h->B = l.B;
     h->NW = l.NW;
-    h->NWT = words_per_thread(l.NW);
+    h->NWT = words_per_thread(l.NW, params->N);
     h->S_pad = l.S_pad;
     h->cap = l.cap;
     h->ncb = l.ncb;
@@ -956,7 +964,7 @@ int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n
         if (t_max[i] < 0 || t_max[i] > kMaxSweeps) return RSOS_EINVAL;
         if (ps[i].surfaces > 1 && ps[i].engine == 0) {
             const int NW = (ps[i].surfaces + 31) / 32;
-            if (NW / words_per_thread(NW) <= 32) ps[i].engine = 2;
+            if (NW / words_per_thread(NW, ps[i].N) <= 32) ps[i].engine = 2;
         }
         size_t bytes = 0;
         const int rc = rsos_required_bytes(&ps[i], &bytes);
