@@ -120,27 +120,63 @@ __global__ void __launch_bounds__(256) column_walk_kernel(JobDev J, const int32_
     }
     if (valid && y0 < y1) {
         const size_t row_stride = (size_t)T * nT * B * J.NW;  // words per lattice row
-        size_t idx = plane_word(J, site_record(J, x, y0), 0, w);
-        uint32_t wv[4] = {0u, 0u, 0u, 0u};
-        for (int b = 0; b < B; ++b) wv[b] = J.planes[idx + (size_t)b * J.NW] >> (lg * 8);
+        const uint32_t* base = J.planes + plane_word(J, site_record(J, x, y0), 0, w);
+        const int sh = lg * 8;
+        // lane k's residue from the plane words of one site (bits sh + k)
+        auto residues = [&](const uint32_t (&wv)[4], int (&v)[8]) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int v = 0;
-            for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> k) & 1u) << b;
-            vprev[k] = v;
+            for (int k = 0; k < 8; ++k) {
+                int a = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (b < B) a |= (int)((wv[b] >> (sh + k)) & 1u) << b;
+                v[k] = a;
+            }
+        };
+        const int hs = 32 - B;  // B-bit two's complement difference by shifts
+        {
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            for (int b = 0; b < B; ++b) wv[b] = base[(size_t)b * J.NW];
+            residues(wv, vprev);
         }
-        // rows y0+1 .. y1 (row y1, if inside the lattice, only closes Delta)
+        // Rows y0+1 .. y1-1 contribute to the sums; row y1 (if inside the
+        // lattice) only closes the segment's difference.  Eight rows' words
+        // are loaded before any is decoded (memory-level parallelism).
         const int ylast = y1 < L ? y1 : L - 1;
-        for (int y = y0 + 1; y <= ylast; ++y) {
-            idx += row_stride;
-            for (int b = 0; b < B; ++b) wv[b] = J.planes[idx + (size_t)b * J.NW] >> (lg * 8);
+        int y = y0 + 1;
+        for (; y + 7 <= ylast; y += 8) {
+            uint32_t wv[8][4];
+#pragma unroll
+            for (int u8 = 0; u8 < 8; ++u8)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    wv[u8][b] = b < B ? __ldg(base + (size_t)(y - y0 + u8) * row_stride + (size_t)b * J.NW) : 0u;
+#pragma unroll
+            for (int u8 = 0; u8 < 8; ++u8) {
+                int v[8];
+                residues(wv[u8], v);
+                const bool inside = y + u8 < y1;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    r[k] += ((v[k] - vprev[k]) << hs) >> hs;
+                    vprev[k] = v[k];
+                    if (inside) {
+                        s1[k] += r[k];
+                        s2[k] += (long long)r[k] * r[k];
+                    }
+                }
+            }
+        }
+        for (; y <= ylast; ++y) {
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            for (int b = 0; b < B; ++b) wv[b] = base[(size_t)(y - y0) * row_stride + (size_t)b * J.NW];
+            int v[8];
+            residues(wv, v);
             const bool inside = y < y1;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                int v = 0;
-                for (int b = 0; b < B; ++b) v |= (int)((wv[b] >> k) & 1u) << b;
-                r[k] += residue_diff(vprev[k], v, B);
-                vprev[k] = v;
+                r[k] += ((v[k] - vprev[k]) << hs) >> hs;
+                vprev[k] = v[k];
                 if (inside) {
                     s1[k] += r[k];
                     s2[k] += (long long)r[k] * r[k];
