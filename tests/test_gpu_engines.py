@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("L,N,S,T,t_end", [
     (64, 1, 64, 8, 40), (128, 2, 64, 8, 25), (64, 4, 32, 8, 30), (32, 1, 64, 4, 40),
     (16, 3, 96, 2, 40), (64, 7, 128, 16, 10), (8, 1, 64, 8, 30), (24, 2, 32, 8, 30),
+    (16, 2, 2048, 8, 12),  # 64 lane words: uint64 words with 3 planes, 32 threads per tile
 ])
 def test_persistent_engine_matches_oracle(L, N, S, T, t_end):
     times = sorted({0, 1, 3, t_end // 2, t_end})
@@ -36,6 +37,23 @@ def test_engines_bit_identical_full_size():
     assert (a[1] == b[1]).all() and (a[2] == b[2]).all()
     for j in (0, 40):
         assert np.array_equal(a[4][j], b[4][j])
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_execution_geometry_is_invisible(N, monkeypatch):
+    """Word width per thread, tiles per lane and phase lag change only how the
+    work is scheduled: sums and heights must not move."""
+    kw = dict(L=256, N=N, S=64, T=8, seed=17, times=[0, 2, 9], t_end=9, height_lanes=[0, 33, 63], engine=2)
+    base = gpu_run(**kw)
+    for env in ({"RSOS_WORDS_PER_THREAD": "1"}, {"RSOS_TILES_PER_LANE": "1"}, {"RSOS_TILES_PER_LANE": "3"},
+                {"RSOS_PHASE_LAG": "2"}, {"RSOS_PHASE_LAG": "40"}):
+        with monkeypatch.context() as m:
+            for k, v in env.items():
+                m.setenv(k, v)
+            other = gpu_run(**kw)
+        assert (base[1] == other[1]).all() and (base[2] == other[2]).all(), env
+        for j in (0, 33, 63):
+            assert np.array_equal(base[4][j], other[4][j]), (env, j)
 
 
 def test_timeout_is_reported_and_gpu_stays_usable():
