@@ -112,14 +112,19 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus: int):
+    """Ranks from the torchrun environment; one process group for the
+    timing reductions (NCCL with GPUs, gloo on a host without)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -128,9 +133,16 @@ def dist_max(value: float, world: int) -> float:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(attempts_per_rank_step: float, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank ran ``steps`` jobs of the same size;
+    the slowest rank's time bounds the job."""
+    return attempts_per_rank_step * world * steps / (max_ms / 1e3)
 
 
 def barrier(world: int):
@@ -221,8 +233,8 @@ def run_gpu(args):
     e2e_s = dist_max(time.perf_counter() - t0, world)
 
     attempts = float(L) * L * S * sweeps
-    value = attempts * world * args.steps / (dev_ms / 1e3)
-    e2e_value = attempts * world * e2e_steps / e2e_s
+    value = aggregate_rate(attempts, world, args.steps, dev_ms)
+    e2e_value = aggregate_rate(attempts, world, e2e_steps, e2e_s * 1e3)
     peaks, peak_src = measured_peaks()
     alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S * n_kernel_sweeps  # per launch
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
