@@ -123,6 +123,27 @@ int rsos_schedule(rsos_handle* h, const int64_t* times, int32_t n);
 int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* sum_h2, double* w2,
                      int32_t cap, int32_t* n_out, void* stream);
 
+/* Height-distribution moments (section III.C: skewness and kurtosis of the
+ * heights in the steady state need the third and fourth central moments).
+ * rsos_set_moments(h, 1): every later measurement (scheduled or rsos_moments)
+ * also records sum h^3 and sum h^4 per surface, exactly; 0 returns to
+ * sum h and sum h^2 only (the cheaper measurement).  RSOS_EINVAL for NULL or
+ * on not 0/1. */
+int rsos_set_moments(rsos_handle* h, int32_t on);
+
+/* Measure now with moments: sums[S][8] (host, caller-owned) receives per
+ * surface sum h^k for k = 1, 2, 3, 4, each as a two's-complement 128-bit
+ * integer (low 64 bits, then high 64 bits); *t_out = t (nullable).
+ * Synchronises the stream. */
+int rsos_moments(rsos_handle* h, int64_t* sums, int64_t* t_out, void* stream);
+
+/* The measured series with moments: times[cap] (nullable), sums[cap][S][8] as
+ * for rsos_moments, has[cap] (nullable) = 1 where the row was measured with
+ * moments on (elsewhere words 4..7 of each surface are 0).  *n_out receives
+ * min(cap, measurements so far).  Synchronises the stream. */
+int rsos_read_moments(rsos_handle* h, int64_t* times, int64_t* sums, int8_t* has, int32_t cap, int32_t* n_out,
+                      void* stream);
+
 /* Absolute heights of one surface at the current time into host_LxL
  * (row-major, x fastest, int64 [L*L]).  Synchronises the stream. */
 int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream);

@@ -6,7 +6,8 @@ may import it.  It shares no code with ``paper_1605_02620_gb300`` and imports
 nothing from it.
 
 * ``rsos_oracle.c``  -- Philox-4x32-10, the double-tiling (DT) sweep and the
-  random-sequential (RS) step of Eq. 6 on int64 heights, exact sums (Eq. 2).
+  random-sequential (RS) step of Eq. 6 on int64 heights, exact sums (Eq. 2)
+  and power sums up to the fourth (height-distribution moments, §III.C).
 * ``enumerate.py``   -- exact Markov-chain enumeration on tiny lattices.
 
 The C file is compiled with gcc on first use (``build()``).
@@ -62,6 +63,8 @@ def _load():
             lib.orc_sweeps.restype = ctypes.c_int
             lib.orc_sums.argtypes = [i64p, ctypes.c_int32, ctypes.c_int32, i64p, i64p, u64p]
             lib.orc_sums.restype = None
+            lib.orc_power_sums.argtypes = [i64p, ctypes.c_int32, ctypes.c_int32, i64p]
+            lib.orc_power_sums.restype = None
             lib.orc_max_step.argtypes = [i64p, ctypes.c_int32, ctypes.c_int32, i64p]
             lib.orc_max_step.restype = None
             _lib = lib
@@ -171,6 +174,28 @@ def sums(h: np.ndarray):
     return [int(v) for v in s1], [(int(a) << 64) + int(b) for a, b in zip(hi, lo)]
 
 
+def power_sums(h: np.ndarray):
+    """Exact [sum h, sum h^2, sum h^3, sum h^4] per field as Python ints."""
+    lib = _load()
+    assert h.dtype == np.int64 and h.flags.c_contiguous
+    n, L = h.shape[0], h.shape[1]
+    w = np.zeros((n, 8), dtype=np.int64)
+    lib.orc_power_sums(_ptr(h, ctypes.c_int64), L, n, _ptr(w, ctypes.c_int64))
+    return [[int(r[2 * k]) % (1 << 64) + (int(r[2 * k + 1]) << 64) for k in range(4)] for r in w]
+
+
+def central_moments(ps, L: int):
+    """Central moments (Phi^2, Phi^3, Phi^4) of one field's height distribution
+    from its exact power sums (section III.C), as exact fractions."""
+    from fractions import Fraction
+    n = L * L
+    m1, m2, m3, m4 = (Fraction(v, n) for v in ps)
+    c2 = m2 - m1 * m1
+    c3 = m3 - 3 * m1 * m2 + 2 * m1 ** 3
+    c4 = m4 - 4 * m1 * m3 + 6 * m1 * m1 * m2 - 3 * m1 ** 4
+    return c2, c3, c4
+
+
 def width2(sum_h: int, sum_h2: int, L: int) -> float:
     """Eq. 2: W^2 = sum h^2 / L^2 - (sum h / L^2)^2, from exact integers."""
     area = L * L
@@ -185,14 +210,15 @@ def max_step(h: np.ndarray) -> np.ndarray:
     return out
 
 
-def run_series(p: Params, lanes, times, rs: bool = False, threads: int | None = None):
+def run_series(p: Params, lanes, times, rs: bool = False, threads: int | None = None, powers: bool = False):
     """Run from the flat start and record exact sums at each time in ``times``
     (completed sweeps, ascending; 0 = the flat start).  Returns
-    (times, sum_h[len(times)][lanes], sum_h2[...], final heights)."""
+    (times, sum_h[len(times)][lanes], sum_h2[...], final heights), and with
+    ``powers`` also the power sums [len(times)][lanes][4] (power_sums)."""
     lanes = list(lanes)
     h = flat(p.L, len(lanes))
     t = 0
-    out_s1, out_s2 = [], []
+    out_s1, out_s2, out_p = [], [], []
     for T in times:
         if T < t:
             raise ValueError("times must be ascending")
@@ -202,4 +228,8 @@ def run_series(p: Params, lanes, times, rs: bool = False, threads: int | None = 
         s1, s2 = sums(h)
         out_s1.append(s1)
         out_s2.append(s2)
+        if powers:
+            out_p.append(power_sums(h))
+    if powers:
+        return list(times), out_s1, out_s2, h, out_p
     return list(times), out_s1, out_s2, h

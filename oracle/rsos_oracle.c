@@ -274,6 +274,32 @@ void orc_sums(const int64_t* h, int32_t L, int32_t n_lanes, int64_t* sum_h,
     }
 }
 
+/*
+ * Exact power sums sum h^k, k = 1..4, per field (the raw moments behind the
+ * height distribution's skewness and kurtosis, section III.C), accumulated in
+ * 128-bit integers: out[8 m + 2 (k-1)] = low 64 bits, out[8 m + 2 k - 1] =
+ * high 64 bits (two's complement).
+ */
+void orc_power_sums(const int64_t* h, int32_t L, int32_t n_lanes, int64_t* out)
+{
+    const int64_t area = (int64_t)L * L;
+    for (int32_t m = 0; m < n_lanes; ++m) {
+        __int128 s[4] = {0, 0, 0, 0};
+        for (int64_t k = 0; k < area; ++k) {
+            const __int128 v = h[m * area + k];
+            __int128 p = v;
+            for (int j = 0; j < 4; ++j) {
+                s[j] += p;
+                p *= v;
+            }
+        }
+        for (int j = 0; j < 4; ++j) {
+            out[8 * m + 2 * j] = (int64_t)(uint64_t)s[j];
+            out[8 * m + 2 * j + 1] = (int64_t)(s[j] >> 64);
+        }
+    }
+}
+
 /* Largest |h(x) - h(n)| over all nearest-neighbour pairs of each field. */
 void orc_max_step(const int64_t* h, int32_t L, int32_t n_lanes, int64_t* out)
 {

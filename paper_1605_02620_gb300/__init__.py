@@ -23,7 +23,8 @@ __all__ = [
     "rsos_schedule", "rsos_read_series", "rsos_heights", "rsos_time", "rsos_free", "rsos_strerror",
     "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc", "rsos_advance",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
-    "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "library_path",
+    "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "rsos_set_moments", "rsos_moments",
+    "rsos_read_moments", "library_path",
 ]
 
 RSOS_OK = 0
@@ -83,6 +84,9 @@ def _load():
             "rsos_schedule": [vp, P(i64), i32],
             "rsos_read_series": [vp, P(i64), P(i64), P(i64), P(ctypes.c_double), i32, P(i32), vp],
             "rsos_heights": [vp, i32, P(i64), vp],
+            "rsos_set_moments": [vp, i32],
+            "rsos_moments": [vp, P(i64), P(i64), vp],
+            "rsos_read_moments": [vp, P(i64), P(i64), P(ctypes.c_int8), i32, P(i32), vp],
             "rsos_time": [vp, P(i64)],
             "rsos_selftest_timeout": [vp, i64, vp],
             "rsos_launches": [vp, P(i64)],
@@ -188,6 +192,40 @@ def rsos_read_series(h, surfaces: int, cap: int, stream=None, allow_overflow: bo
            "rsos_read_series", allow=(RSOS_EOVERFLOW,) if allow_overflow else ())
     k = n.value
     return times[:k], s1[:k], s2[:k], w2[:k]
+
+
+def _int128_rows(words: np.ndarray) -> list:
+    """[..., 8] int64 words (four 128-bit (lo, hi) pairs) -> nested lists of
+    four Python ints: sum h, sum h^2, sum h^3, sum h^4."""
+    flat = words.reshape(-1, 8)
+    out = [[int(r[2 * k]) % (1 << 64) + (int(r[2 * k + 1]) << 64) for k in range(4)] for r in flat]
+    return np.array(out, dtype=object).reshape(words.shape[:-1] + (4,))
+
+
+def rsos_set_moments(h, on: bool = True) -> None:
+    _check(_load().rsos_set_moments(h, 1 if on else 0), "rsos_set_moments")
+
+
+def rsos_moments(h, surfaces: int, stream=None):
+    """Measure now with moments: (t, sums[S, 4]) with exact Python ints
+    sum h, sum h^2, sum h^3, sum h^4 per surface."""
+    words = np.zeros((surfaces, 8), dtype=np.int64)
+    t = ctypes.c_int64()
+    _check(_load().rsos_moments(h, _p(words, ctypes.c_int64), ctypes.byref(t), _stream(stream)), "rsos_moments")
+    return t.value, _int128_rows(words)
+
+
+def rsos_read_moments(h, surfaces: int, cap: int, stream=None):
+    """The series with moments: (times[n], sums[n, S, 4] exact Python ints,
+    has[n]: rows measured with moments on)."""
+    times = np.zeros(cap, dtype=np.int64)
+    words = np.zeros((cap, surfaces, 8), dtype=np.int64)
+    has = np.zeros(cap, dtype=np.int8)
+    n = ctypes.c_int32()
+    _check(_load().rsos_read_moments(h, _p(times, ctypes.c_int64), _p(words, ctypes.c_int64), _p(has, ctypes.c_int8),
+                                     int(cap), ctypes.byref(n), _stream(stream)), "rsos_read_moments")
+    k = n.value
+    return times[:k], _int128_rows(words[:k]), has[:k].astype(bool)
 
 
 def rsos_heights(h, surface: int, L: int, stream=None) -> np.ndarray:

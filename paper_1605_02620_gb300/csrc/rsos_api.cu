@@ -29,9 +29,11 @@ struct rsos_handle {
     int32_t* row0;
     int64_t* partial;
     int ncb;
-    int64_t* rec;  // [cap + 1][S_pad][4]; the last row is rsos_width's scratch
+    int64_t* rec;  // [cap + 1][S_pad][kRecWords]; the last row is rsos_width's scratch
     int cap;
     std::vector<int64_t> series_t;
+    std::vector<char> series_mom;  // row m also holds sum h^3, sum h^4
+    bool moments;                  // measurements record sum h^3, sum h^4 too
     int64_t t;
     std::vector<int64_t> sched;
     size_t sched_pos;
@@ -51,6 +53,10 @@ struct rsos_handle {
 namespace {
 
 constexpr int64_t kMaxSweeps = 0xFFFFFFFFll;
+
+// int64 words per surface and measurement in the series buffer: sum h^k for
+// k = 1..4 as 128-bit (lo, hi) pairs (k = 3, 4 only when moments are on).
+constexpr int kRecWords = 8;
 
 // CUDA error of the last failed rsos_init on this thread (no handle exists).
 thread_local int g_init_cuda_err = 0;
@@ -142,8 +148,8 @@ Layout layout_of(const rsos_params* p)
     l.planes = align256(l.plain ? L * L * 4 : (size_t)l.B * L * L * l.NW * 4);
     l.h00 = align256((size_t)l.S_pad * 8);
     l.row0 = l.plain ? 0 : align256((size_t)l.S_pad * L * 4);
-    l.partial = align256((size_t)l.ncb * l.S_pad * 2 * 8);
-    l.rec = align256((size_t)(l.cap + 1) * l.S_pad * 4 * 8);
+    l.partial = align256((size_t)l.ncb * l.S_pad * 6 * 8);  // moments need 6 words per entry
+    l.rec = align256((size_t)(l.cap + 1) * l.S_pad * kRecWords * 8);
     const int nT = p->L / l.T;
     // Auto engine: the persistent dataflow engine for multisurface jobs with
     // at least 8 tile rows, one launch per phase otherwise.
@@ -196,11 +202,13 @@ double width2_from_sums(__int128 sh, __int128 sh2, int64_t L)
     return (double)centred / a - m * m;
 }
 
-int measure_into(rsos_handle* h, int row, cudaStream_t s)
+int measure_into(rsos_handle* h, int row, cudaStream_t s, bool moments)
 {
     h->launches += h->plain ? 2 : 3;
-    return fail_cuda(h, rsos::launch_measure(h->J, h->plain, h->S_pad, h->row0, h->partial, h->ncb,
-                                             h->rec + (size_t)row * h->S_pad * 4, s));
+    int64_t* dst = h->rec + (size_t)row * h->S_pad * kRecWords;
+    return fail_cuda(h, moments ? rsos::launch_moments(h->J, h->plain, h->S_pad, h->row0, h->partial, h->ncb, dst, s)
+                                : rsos::launch_measure(h->J, h->plain, h->S_pad, h->row0, h->partial, h->ncb, dst,
+                                                       kRecWords, s));
 }
 
 int measure_due(rsos_handle* h, cudaStream_t s)
@@ -208,9 +216,10 @@ int measure_due(rsos_handle* h, cudaStream_t s)
     while (h->sched_pos < h->sched.size() && h->sched[h->sched_pos] <= h->t) {
         if (h->sched[h->sched_pos] == h->t) {
             if ((int)h->series_t.size() >= h->cap) return RSOS_ERANGE;
-            const int rc = measure_into(h, (int)h->series_t.size(), s);
+            const int rc = measure_into(h, (int)h->series_t.size(), s, h->moments);
             if (rc) return rc;
             h->series_t.push_back(h->t);
+            h->series_mom.push_back(h->moments ? 1 : 0);
         }
         ++h->sched_pos;
     }
@@ -295,7 +304,7 @@ void convert_row(const rsos_handle* h, const int64_t* rec_row, int64_t* sum_h, i
                  bool* overflow)
 {
     for (int j = 0; j < h->p.surfaces; ++j) {
-        const int64_t* r = rec_row + (size_t)j * 4;
+        const int64_t* r = rec_row + (size_t)j * kRecWords;
         if (sum_h) {
             if (fits64(r[0], r[1])) sum_h[j] = r[0];
             else { sum_h[j] = INT64_MIN; *overflow = true; }
@@ -418,6 +427,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->t = 0;
     h->sched_pos = 0;
     h->sticky = RSOS_OK;
+    h->moments = false;
     h->cuda_err = 0;
     h->launches = l.persist_on ? 3 : 1;
     h->smem_budget = 113 * 1024;
@@ -559,10 +569,10 @@ int rsos_width(rsos_handle* h, int64_t* sum_h, int64_t* sum_h2, double* w2, int6
     cudaStream_t s = as_stream(stream);
     int rc = check_device_error(h, s);
     if (rc) return rc;
-    rc = measure_into(h, h->cap, s);
+    rc = measure_into(h, h->cap, s, false);
     if (rc) return rc;
-    std::vector<int64_t> host((size_t)h->S_pad * 4);
-    cudaError_t e = cudaMemcpyAsync(host.data(), h->rec + (size_t)h->cap * h->S_pad * 4, host.size() * 8,
+    std::vector<int64_t> host((size_t)h->S_pad * kRecWords);
+    cudaError_t e = cudaMemcpyAsync(host.data(), h->rec + (size_t)h->cap * h->S_pad * kRecWords, host.size() * 8,
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(h, e);
@@ -594,7 +604,7 @@ int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* su
     const int n = std::min<int>(cap, (int)h->series_t.size());
     *n_out = n;
     if (n == 0) return RSOS_OK;
-    std::vector<int64_t> host((size_t)n * h->S_pad * 4);
+    std::vector<int64_t> host((size_t)n * h->S_pad * kRecWords);
     cudaError_t e = cudaMemcpyAsync(host.data(), h->rec, host.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(h, e);
@@ -602,10 +612,64 @@ int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* su
     const int S = h->p.surfaces;
     for (int m = 0; m < n; ++m) {
         if (times) times[m] = h->series_t[m];
-        convert_row(h, host.data() + (size_t)m * h->S_pad * 4, sum_h ? sum_h + (size_t)m * S : nullptr,
+        convert_row(h, host.data() + (size_t)m * h->S_pad * kRecWords, sum_h ? sum_h + (size_t)m * S : nullptr,
                     sum_h2 ? sum_h2 + (size_t)m * S : nullptr, w2 ? w2 + (size_t)m * S : nullptr, &overflow);
     }
     return overflow ? RSOS_EOVERFLOW : RSOS_OK;
+}
+
+int rsos_set_moments(rsos_handle* h, int32_t on)
+{
+    if (!h || (on != 0 && on != 1)) return RSOS_EINVAL;
+    h->moments = on != 0;
+    return RSOS_OK;
+}
+
+int rsos_moments(rsos_handle* h, int64_t* sums, int64_t* t_out, void* stream)
+{
+    if (!h || !sums) return RSOS_EINVAL;
+    if (h->sticky) return h->sticky;
+    cudaStream_t s = as_stream(stream);
+    int rc = check_device_error(h, s);
+    if (rc) return rc;
+    rc = measure_into(h, h->cap, s, true);
+    if (rc) return rc;
+    std::vector<int64_t> host((size_t)h->S_pad * kRecWords);
+    cudaError_t e = cudaMemcpyAsync(host.data(), h->rec + (size_t)h->cap * h->S_pad * kRecWords, host.size() * 8,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    std::copy(host.begin(), host.begin() + (size_t)h->p.surfaces * kRecWords, sums);
+    if (t_out) *t_out = h->t;
+    return RSOS_OK;
+}
+
+int rsos_read_moments(rsos_handle* h, int64_t* times, int64_t* sums, int8_t* has, int32_t cap, int32_t* n_out,
+                      void* stream)
+{
+    if (!h || cap < 0 || !n_out || !sums) return RSOS_EINVAL;
+    if (h->sticky) return h->sticky;
+    cudaStream_t s = as_stream(stream);
+    const int rc = check_device_error(h, s);
+    if (rc) return rc;
+    const int n = std::min<int>(cap, (int)h->series_t.size());
+    *n_out = n;
+    if (n == 0) return RSOS_OK;
+    std::vector<int64_t> host((size_t)n * h->S_pad * kRecWords);
+    cudaError_t e = cudaMemcpyAsync(host.data(), h->rec, host.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const int S = h->p.surfaces;
+    for (int m = 0; m < n; ++m) {
+        const bool mom = h->series_mom[m] != 0;
+        if (times) times[m] = h->series_t[m];
+        if (has) has[m] = mom ? 1 : 0;
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < kRecWords; ++k)
+                sums[((size_t)m * S + j) * kRecWords + k] =
+                    (mom || k < 4) ? host[((size_t)m * h->S_pad + j) * kRecWords + k] : 0;
+    }
+    return RSOS_OK;
 }
 
 int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream)

@@ -64,10 +64,16 @@ RSOS_DECLARE_PERSIST(4)
 RSOS_DECLARE_PERSIST(8)
 #undef RSOS_DECLARE_PERSIST
 
-// Measurement (Eq. 2 numerators), exact: fills rec[S_pad][4] with the 128-bit
-// sum h and sum h^2 of every lane as (lo, hi) int64 pairs.
+// Measurement (Eq. 2 numerators), exact: the 128-bit sum h and sum h^2 of
+// every lane as (lo, hi) int64 pairs into rec[lane * rec_stride + 0..3]
+// (partial: measure_blocks x S_pad x 2 int64).
 cudaError_t launch_measure(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial,
-                           int ncb_capacity, int64_t* rec, cudaStream_t s);
+                           int ncb_capacity, int64_t* rec, int rec_stride, cudaStream_t s);
+// Power sums for the height distribution's moments: sum h^k, k = 1..4, as
+// 128-bit (lo, hi) pairs into rec8[lane * 8 ...] (partial: measure_blocks x
+// S_pad x 6 int64).
+cudaError_t launch_moments(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial,
+                           int ncb_capacity, int64_t* rec8, cudaStream_t s);
 // Number of column blocks the measurement needs (partial buffer rows).
 int measure_blocks(const JobDev& J, bool plain);
 // Absolute heights of one lane into out[L*L] (int64).

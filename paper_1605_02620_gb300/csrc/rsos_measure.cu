@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) plain_sum_kernel(const int32_t* __restric
 // absolute sums with h00.
 __global__ void __launch_bounds__(128) finalize_kernel(const int64_t* __restrict__ partial, int nrows, int S_pad,
                                                        int L, const int64_t* __restrict__ h00,
-                                                       int64_t* __restrict__ rec)
+                                                       int64_t* __restrict__ rec, int rec_stride)
 {
     __shared__ __int128 a1[128], a2[128];
     const int lane = blockIdx.x;
@@ -285,10 +285,227 @@ __global__ void __launch_bounds__(128) finalize_kernel(const int64_t* __restrict
     const __int128 area = (__int128)L * L;
     const __int128 sh = area * h0 + s1;
     const __int128 sh2 = area * h0 * h0 + 2 * h0 * s1 + s2;
-    rec[(size_t)lane * 4 + 0] = (int64_t)(uint64_t)sh;
-    rec[(size_t)lane * 4 + 1] = (int64_t)(sh >> 64);
-    rec[(size_t)lane * 4 + 2] = (int64_t)(uint64_t)sh2;
-    rec[(size_t)lane * 4 + 3] = (int64_t)(sh2 >> 64);
+    rec[(size_t)lane * rec_stride + 0] = (int64_t)(uint64_t)sh;
+    rec[(size_t)lane * rec_stride + 1] = (int64_t)(sh >> 64);
+    rec[(size_t)lane * rec_stride + 2] = (int64_t)(uint64_t)sh2;
+    rec[(size_t)lane * rec_stride + 3] = (int64_t)(sh2 >> 64);
+}
+
+// ---- Third and fourth power sums (height-distribution skewness and
+// kurtosis, section III.C).  Same walk as column_walk_kernel, also carrying
+// sum r^3 (int64: |r| <= L/8 * N in a segment) and sum r^4 (128-bit); the
+// segments and the row-0 offsets combine by binomial expansion in 128 bits.
+__device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o)
+{
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, o);
+    const long long hi = __shfl_down_sync(0xffffffffu, (long long)(v >> 64), o);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+
+// Per (column block, lane): sum over the block's columns of rel^k, k = 1..4,
+// into partial[(cb * S_pad + lane) * 6 + ...] = t1, t2, t3 lo, t3 hi, t4 lo, t4 hi.
+__global__ void __launch_bounds__(256) column_moments_kernel(JobDev J, const int32_t* __restrict__ row0, int S_pad,
+                                                             int64_t* __restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char msm[];
+    // [kSeg][8][32] each: D, S1 (int32), S2, S3 (int64), S4 (int128)
+    int32_t* sD = reinterpret_cast<int32_t*>(msm);
+    int32_t* sS1 = sD + kSeg * 8 * 32;
+    long long* sS2 = reinterpret_cast<long long*>(sS1 + kSeg * 8 * 32);
+    long long* sS3 = sS2 + kSeg * 8 * 32;
+    __int128* sS4 = reinterpret_cast<__int128*>(sS3 + kSeg * 8 * 32);
+    const int lg = blockIdx.x, cb = blockIdx.y, w = blockIdx.z;
+    const int T = J.T, nT = J.nT, L = J.L, B = J.B;
+    const int u = cb % T;
+    const int col = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int m = (cb / T) * 32 + col;
+    const bool valid = m < nT;
+    const int x = m * T + u;
+    const int RL = (L + kSeg - 1) / kSeg;
+    const int y0 = min(L, seg * RL), y1 = min(L, y0 + RL);
+    int r[8], s1[8], vprev[8];
+    long long s2[8], s3[8];
+    __int128 s4[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        r[k] = 0;
+        s1[k] = 0;
+        s2[k] = 0;
+        s3[k] = 0;
+        s4[k] = 0;
+        vprev[k] = 0;
+    }
+    if (valid && y0 < y1) {
+        const size_t row_stride = (size_t)T * nT * B * J.NW;
+        const uint32_t* base = J.planes + plane_word(J, site_record(J, x, y0), 0, w);
+        const int sh = lg * 8, hs = 32 - B;
+        auto residues = [&](const uint32_t* wv, int* v) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int a = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (b < B) a |= (int)((wv[b] >> (sh + k)) & 1u) << b;
+                v[k] = a;
+            }
+        };
+        {
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            for (int b = 0; b < B; ++b) wv[b] = base[(size_t)b * J.NW];
+            residues(wv, vprev);
+        }
+        const int ylast = y1 < L ? y1 : L - 1;
+        for (int y = y0 + 1; y <= ylast; ++y) {
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            for (int b = 0; b < B; ++b) wv[b] = __ldg(base + (size_t)(y - y0) * row_stride + (size_t)b * J.NW);
+            int v[8];
+            residues(wv, v);
+            const bool inside = y < y1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                r[k] += ((v[k] - vprev[k]) << hs) >> hs;
+                vprev[k] = v[k];
+                if (inside) {
+                    const long long rr = (long long)r[k] * r[k];
+                    s1[k] += r[k];
+                    s2[k] += rr;
+                    s3[k] += rr * r[k];
+                    s4[k] += (__int128)(rr * rr);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = (seg * 8 + k) * 32 + col;
+        sD[i] = r[k];
+        sS1[i] = s1[k];
+        sS2[i] = s2[k];
+        sS3[i] = s3[k];
+        sS4[i] = s4[k];
+    }
+    __syncthreads();
+    if (seg != 0) return;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const int lane = lg * 8 + k;
+        __int128 t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+        if (valid) {
+            // segments in order: a segment of n rows at offset o adds
+            // sum (o + r)^j, expanded binomially
+            __int128 off = 0;
+            for (int sg = 0; sg < kSeg; ++sg) {
+                const int a0 = min(L, sg * RL), a1 = min(L, a0 + RL);
+                const __int128 n = a1 - a0;
+                if (n <= 0) break;
+                const int i = (sg * 8 + k) * 32 + col;
+                const __int128 q1 = sS1[i], q2 = sS2[i], q3 = sS3[i], q4 = sS4[i];
+                const __int128 o2 = off * off, o3 = o2 * off;
+                t1 += n * off + q1;
+                t2 += n * o2 + 2 * off * q1 + q2;
+                t3 += n * o3 + 3 * o2 * q1 + 3 * off * q2 + q3;
+                t4 += n * o3 * off + 4 * o3 * q1 + 6 * o2 * q2 + 4 * off * q3 + q4;
+                off += sD[i];
+            }
+            // shift the column by its row-0 value rel(x, 0)
+            const __int128 c = row0[(size_t)(w * 32 + lane) * L + x];
+            const __int128 c2 = c * c, c3 = c2 * c, nL = L;
+            t4 += nL * c3 * c + 4 * c3 * t1 + 6 * c2 * t2 + 4 * c * t3;
+            t3 += nL * c3 + 3 * c2 * t1 + 3 * c * t2;
+            t2 += nL * c2 + 2 * c * t1;
+            t1 += nL * c;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            t1 += shfl_down_i128(t1, o);
+            t2 += shfl_down_i128(t2, o);
+            t3 += shfl_down_i128(t3, o);
+            t4 += shfl_down_i128(t4, o);
+        }
+        if (col == 0) {
+            int64_t* out = partial + ((size_t)cb * S_pad + (size_t)w * 32 + lane) * 6;
+            out[0] = (int64_t)t1;  // |t1|, |t2| of 32 columns fit 64 bits
+            out[1] = (int64_t)t2;
+            out[2] = (int64_t)(uint64_t)t3;
+            out[3] = (int64_t)(t3 >> 64);
+            out[4] = (int64_t)(uint64_t)t4;
+            out[5] = (int64_t)(t4 >> 64);
+        }
+    }
+}
+
+constexpr size_t kMomentsSmem = (size_t)kSeg * 8 * 32 * (4 + 4 + 8 + 8 + 16);
+
+// Plain path: power sums of the int32 heights, six words per block.
+__global__ void __launch_bounds__(256) plain_moments_kernel(const int32_t* __restrict__ h, long long n,
+                                                            int64_t* __restrict__ partial)
+{
+    __int128 a[4] = {0, 0, 0, 0};
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const __int128 v = h[k], v2 = v * v;
+        a[0] += v;
+        a[1] += v2;
+        a[2] += v2 * v;
+        a[3] += v2 * v2;
+    }
+    __shared__ __int128 sa[4][256];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sa[j][threadIdx.x] = a[j];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sa[j][threadIdx.x] += sa[j][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int64_t* out = partial + (size_t)blockIdx.x * 6;
+        out[0] = (int64_t)sa[0][0];
+        out[1] = (int64_t)sa[1][0];
+        out[2] = (int64_t)(uint64_t)sa[2][0];
+        out[3] = (int64_t)(sa[2][0] >> 64);
+        out[4] = (int64_t)(uint64_t)sa[3][0];
+        out[5] = (int64_t)(sa[3][0] >> 64);
+    }
+}
+
+// Per lane: 128-bit totals of sum rel^k over the partial rows, then
+// sum h^k = sum_j C(k, j) h00^(k-j) sum rel^j  (sum rel^0 = L^2), into
+// rec[lane * 8 ...] = sum h, sum h^2, sum h^3, sum h^4 as (lo, hi) pairs.
+__global__ void __launch_bounds__(128) finalize_moments_kernel(const int64_t* __restrict__ partial, int nrows,
+                                                               int S_pad, int L, const int64_t* __restrict__ h00,
+                                                               int64_t* __restrict__ rec)
+{
+    __shared__ __int128 acc[4][128];
+    const int lane = blockIdx.x;
+    __int128 s[4] = {0, 0, 0, 0};
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        const int64_t* p = partial + ((size_t)r * S_pad + lane) * 6;
+        s[0] += (__int128)p[0];
+        s[1] += (__int128)p[1];
+        s[2] += (__int128)(((unsigned __int128)(uint64_t)p[3] << 64) | (uint64_t)p[2]);
+        s[3] += (__int128)(((unsigned __int128)(uint64_t)p[5] << 64) | (uint64_t)p[4]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j][threadIdx.x] = s[j];
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j][threadIdx.x] += acc[j][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const __int128 a = h00 ? (__int128)h00[lane] : (__int128)0;
+    const __int128 n = (__int128)L * L, q1 = acc[0][0], q2 = acc[1][0], q3 = acc[2][0], q4 = acc[3][0];
+    const __int128 a2 = a * a, a3 = a2 * a;
+    const __int128 out[4] = {n * a + q1, n * a2 + 2 * a * q1 + q2, n * a3 + 3 * a2 * q1 + 3 * a * q2 + q3,
+                             n * a3 * a + 4 * a3 * q1 + 6 * a2 * q2 + 4 * a * q3 + q4};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        rec[(size_t)lane * 8 + 2 * j] = (int64_t)(uint64_t)out[j];
+        rec[(size_t)lane * 8 + 2 * j + 1] = (int64_t)(out[j] >> 64);
+    }
 }
 
 // Heights of one lane: thread per column, walking down y from row 0.
@@ -329,18 +546,37 @@ int measure_blocks(const JobDev& J, bool plain)
 }
 
 cudaError_t launch_measure(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial, int ncb_capacity,
-                           int64_t* rec, cudaStream_t s)
+                           int64_t* rec, int rec_stride, cudaStream_t s)
 {
     const int ncb = measure_blocks(J, plain);
     if (ncb > ncb_capacity) return cudaErrorInvalidValue;
     if (plain) {
         plain_sum_kernel<<<ncb, 256, 0, s>>>(J.heights, (long long)J.L * J.L, partial);
-        finalize_kernel<<<1, 128, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec);
+        finalize_kernel<<<1, 128, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec, rec_stride);
         return cudaGetLastError();
     }
     row0_prefix_kernel<<<J.NW, 1024, 0, s>>>(J, row0);
     column_walk_kernel<<<dim3(4, ncb, J.NW), 256, 0, s>>>(J, row0, S_pad, partial);
-    finalize_kernel<<<S_pad, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec);
+    finalize_kernel<<<S_pad, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec, rec_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const JobDev& J, bool plain, int S_pad, int32_t* row0, int64_t* partial,
+                           int ncb_capacity, int64_t* rec8, cudaStream_t s)
+{
+    const int ncb = measure_blocks(J, plain);
+    if (ncb > ncb_capacity) return cudaErrorInvalidValue;
+    if (plain) {
+        plain_moments_kernel<<<ncb, 256, 0, s>>>(J.heights, (long long)J.L * J.L, partial);
+        finalize_moments_kernel<<<1, 128, 0, s>>>(partial, ncb, 1, J.L, nullptr, rec8);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(column_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMomentsSmem);
+    if (e != cudaSuccess) return e;
+    row0_prefix_kernel<<<J.NW, 1024, 0, s>>>(J, row0);
+    column_moments_kernel<<<dim3(4, ncb, J.NW), 256, kMomentsSmem, s>>>(J, row0, S_pad, partial);
+    finalize_moments_kernel<<<S_pad, 128, 0, s>>>(partial, ncb, S_pad, J.L, J.h00, rec8);
     return cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ extern "C" int rsos_width_noalloc(const rsos_params* params, const uint32_t* pla
     int64_t* partial = reinterpret_cast<int64_t*>(p + row0_bytes);
     int64_t* rec = reinterpret_cast<int64_t*>(p + row0_bytes + partial_bytes);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = rsos::launch_measure(J, false, S_pad, row0, partial, ncb, rec, s);
+    cudaError_t e = rsos::launch_measure(J, false, S_pad, row0, partial, ncb, rec, 4, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sums, rec, (size_t)params->surfaces * 4 * 8, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {
