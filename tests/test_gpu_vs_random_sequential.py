@@ -1,0 +1,75 @@
+"""The GPU's double-tiling (DT) dynamics against a true random-sequential (RS)
+oracle (one uniformly random site per attempt, no domains).  The domain
+decomposition lowers the width's amplitude by a few per cent (the N -> inf
+closed forms already differ by the factor 1 - 1/(2a)), so the comparison is
+on what the paper's use of DT rests on: the same growth exponent, curves
+W_DT(t) / W_RS(t) parallel in time, and the same roughness exponent."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1605_02620_gb300 as R
+
+pytestmark = pytest.mark.gpu
+THREADS = min(16, os.cpu_count() or 1)
+
+
+def _gpu_w2(L, S, seed, times):
+    p = R.rsos_params(L=L, N=1, surfaces=S, tile=8, seed=seed, series_capacity=len(times) + 1)
+    h = R.rsos_init(p)
+    try:
+        R.rsos_schedule(h, times)
+        R.rsos_sweep(h, times[-1])
+        return R.rsos_read_series(h, S, len(times) + 1)[3]  # [n_times, S]
+    finally:
+        R.rsos_free(h)
+
+
+def _rs_w2(L, lanes, seed, times):
+    ts, s1, s2, _ = O.run_series(O.Params(L=L, N=1, Tx=8, Ty=8, seed=seed), list(range(lanes)), times, rs=True,
+                                 threads=THREADS)
+    return np.array([[O.width2(a, b, L) for a, b in zip(s1[m], s2[m])] for m in range(len(times))])
+
+
+def _blocks(w2, size):
+    """Block means over surfaces (columns): independent samples of the curve."""
+    n = w2.shape[1] // size
+    return np.stack([w2[:, k * size:(k + 1) * size].mean(axis=1) for k in range(n)])
+
+
+def test_growth_exponent_and_parallel_curves():
+    L, times = 128, [16, 32, 64, 128, 256, 512]
+    dt = _blocks(_gpu_w2(L, 256, 31, times), 8)   # 32 blocks x times
+    rs = _blocks(_rs_w2(L, 64, 32, times), 8)     # 8 blocks x times
+    beff = lambda b: 0.5 * np.log(b[:, 2:5] / b[:, 1:4]).mean(axis=1) / math.log(2.0)  # 32 -> 256
+    bd, br = beff(dt), beff(rs)
+    se = math.sqrt(bd.var(ddof=1) / len(bd) + br.var(ddof=1) / len(br))
+    assert abs(bd.mean() - br.mean()) < 3 * se, (bd.mean(), br.mean(), se)
+    assert 0.20 < bd.mean() < 0.28 and 0.20 < br.mean() < 0.28
+    # amplitude ratio: a few per cent, the same early and late
+    ratio = dt.mean(axis=0) / rs.mean(axis=0)
+    rel = lambda b: b.std(axis=0, ddof=1) / math.sqrt(len(b)) / b.mean(axis=0)
+    dr = ratio * np.sqrt(rel(dt) ** 2 + rel(rs) ** 2)
+    assert np.all(np.abs(ratio - 1) < 0.12), ratio
+    assert abs(ratio[1] - ratio[-2]) < 3 * math.hypot(dr[1], dr[-2]), (ratio, dr)
+
+
+def test_roughness_exponent_matches_rs():
+    sat = {}
+    for L in (16, 32, 64):
+        t_sat = int(12 * L ** 1.61)  # past t_steady ~ L^z
+        times = [t_sat + k * max(1, t_sat // 10) for k in range(11)]
+        dt = _gpu_w2(L, 256, 40 + L, times).mean(axis=0)   # per surface, time-averaged
+        rs = _rs_w2(L, 64, 80 + L, times).mean(axis=0)
+        sat[L] = [(x.mean(), x.std(ddof=1) / math.sqrt(len(x))) for x in (dt, rs)]
+    for a, b in ((16, 32), (32, 64)):
+        al, se = [], []
+        for k in range(2):
+            (wa, ea), (wb, eb) = sat[a][k], sat[b][k]
+            al.append(0.5 * math.log(wb / wa) / math.log(2.0))
+            se.append(0.5 * math.hypot(ea / wa, eb / wb) / math.log(2.0))
+        assert abs(al[0] - al[1]) < 3 * math.hypot(*se), (a, b, al, se)
+        assert all(0.33 < v < 0.45 for v in al), (a, b, al)
