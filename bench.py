@@ -301,7 +301,15 @@ def run_batched(args):
 
     scale = args.batch_scale
     jobs = batched_jobs()
-    params = [R.rsos_params(L=j["L"], N=j["N"], surfaces=j["surfaces"], tile=8, seed=j["seed"], series_capacity=2)
+    # execution geometry per (L, N) from the autotuner (untimed set-up; the
+    # results do not depend on it)
+    geometry = {}
+    for L, N in sorted({(j["L"], j["N"]) for j in jobs}):
+        tuned, _ = R.rsos_autotune(R.rsos_params(L=L, N=N, surfaces=64, tile=8), sweeps=10)
+        geometry[(L, N)] = (tuned.words_per_thread, tuned.tiles_per_lane, tuned.phase_lag)
+    params = [R.rsos_params(L=j["L"], N=j["N"], surfaces=j["surfaces"], tile=8, seed=j["seed"], series_capacity=2,
+                            **dict(zip(("words_per_thread", "tiles_per_lane", "phase_lag"),
+                                       geometry[(j["L"], j["N"])])))
               for j in jobs]
     tmax = [max(1, j["t_max"] // scale) for j in jobs]
     attempts = float(sum(j["L"] * j["L"] * j["surfaces"] * t for j, t in zip(jobs, tmax)))
@@ -342,7 +350,9 @@ def run_batched(args):
     # sweeps), then every job charged at its own rate.
     rates = {}
     for L, N in sorted({(j["L"], j["N"]) for j in jobs}):
-        h = R.rsos_init(R.rsos_params(L=L, N=N, surfaces=64, tile=8, seed=0, series_capacity=2), stream=stream)
+        wpt, tpl, lag = geometry[(L, N)]
+        h = R.rsos_init(R.rsos_params(L=L, N=N, surfaces=64, tile=8, seed=0, series_capacity=2,
+                                      words_per_thread=wpt, tiles_per_lane=tpl, phase_lag=lag), stream=stream)
         R.rsos_sweep(h, 20, stream=stream)
         n = max(20, int(5e10 / (L * L * 64 * (1.0 if N == 1 else 2.0)) / 5))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -359,11 +369,14 @@ def run_batched(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64/u32 (bit-sliced int)", "data": "synthetic",
         "plain_equivalent": {"value": plain_equiv, "unit": "attempts/s", "ratio": value / plain_equiv,
-                             "how": "the same jobs run one at a time, each at its own (L, N) single-job rate",
+                             "how": "the same jobs run one at a time, each at its own (L, N) single-job rate "
+                                    "with the same autotuned geometry",
                              "rates": {f"L{L}_N{N}": r for (L, N), r in rates.items()}},
         "config": {"workload": f"batched: 256 jobs, L in {{256..4096}}, N in {{1,2}}, 64 surfaces, t_max in "
                                f"[1e3,1e4]/{scale} sweeps, PCG64 seed 2016; one multi-job persistent launch per class "
-                               "in a CUDA graph", "jobs": len(jobs), "attempts_per_step": attempts,
+                               "in a CUDA graph; execution geometry per (L, N) from rsos_autotune",
+                   "jobs": len(jobs), "attempts_per_step": attempts,
+                   "geometry": {f"L{L}_N{N}": list(g) for (L, N), g in geometry.items()},
                    "l2": "inputs larger than L2"},
         "clocks": clk, "w2_sample": w2,
     }), flush=True)
@@ -385,10 +398,14 @@ def run_served(args):
                     surfaces=j["surfaces"], arrival=j["arrival"], rid=k) for k, j in enumerate(jobs)]
     stream = torch.cuda.Stream()
     warm = [Request(L=256, N=n, t_max=20, seed=k, surfaces=64, arrival=0.0, rid=k) for k, n in enumerate((1, 2, 3, 4))]
-    Server(hbm_budget=args.serve_budget, stream=stream).run(warm)
+    # warm-up: also tunes every job shape of the stream (cached; untimed)
+    shapes = sorted({(r.L, r.N, r.surfaces) for r in reqs})
+    Server(hbm_budget=args.serve_budget, stream=stream, tune=True).run(
+        warm + [Request(L=L, N=N, t_max=1, seed=0, surfaces=S, arrival=0.0, rid=-1 - k)
+                for k, (L, N, S) in enumerate(shapes)])
     clocks = ClockSampler(0)
     clocks.start()
-    rep = Server(hbm_budget=args.serve_budget, epoch_s=args.serve_epoch, stream=stream).run(reqs)
+    rep = Server(hbm_budget=args.serve_budget, epoch_s=args.serve_epoch, stream=stream, tune=True).run(reqs)
     clk = clocks.stop()
     s = rep.summary()
     print(json.dumps({
@@ -397,7 +414,8 @@ def run_served(args):
         "dtype": "u64/u32 (bit-sliced int)", "data": "synthetic",
         "config": {"workload": f"served: {len(reqs)} Poisson requests at {args.serve_rate}/s, L=2^(8..13), N in 1..4, "
                                f"64 surfaces, t_max in [1e2,1e4]/{args.serve_scale} sweeps, PCG64 seed 2017",
-                   "hbm_budget": args.serve_budget, "epoch_s": args.serve_epoch},
+                   "hbm_budget": args.serve_budget, "epoch_s": args.serve_epoch,
+                   "geometry": "per job shape from rsos_autotune (tuned in the warm-up)"},
         "serve": s, "clocks": clk,
     }), flush=True)
 

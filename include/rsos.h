@@ -68,7 +68,15 @@ typedef struct rsos_batch rsos_batch;
  *                (0 means 1024).
  *   engine       0 auto, 1 one launch per phase, 2 persistent dataflow kernel.
  *                Every engine gives bit-identical results.
- *   seed         Philox key of the job.                                       */
+ *   seed         Philox key of the job.
+ * Execution geometry of the persistent engine (no counterpart in the paper;
+ * results are bit-identical for every choice; 0 = automatic, see
+ * rsos_autotune):
+ *   words_per_thread  32-lane words each thread holds: 1, or 2 (uint64; needs
+ *                an even number of words).
+ *   tiles_per_lane  tiles a lane runs per work item, 1..64.
+ *   phase_lag    slots between consecutive phase fronts of the ticket order,
+ *                >= 2.                                                        */
 typedef struct {
     int32_t L;
     int32_t N;
@@ -79,12 +87,30 @@ typedef struct {
     int32_t series_capacity;
     int32_t engine;
     uint64_t seed;
+    int32_t words_per_thread;
+    int32_t tiles_per_lane;
+    int32_t phase_lag;
 } rsos_params;
 
 /* Bytes of device memory a job needs (lattice planes, h(0,0) per surface,
  * measurement scratch, series buffer).  Returns RSOS_EINVAL for invalid
  * params. */
 int rsos_required_bytes(const rsos_params* params, size_t* bytes);
+
+/* Autotuner of the execution geometry (no counterpart in the paper).  Times
+ * candidate (words_per_thread, tiles_per_lane, phase_lag) settings of the
+ * persistent engine for params' (L, N, surfaces, tile, phase order) on a
+ * scratch job the library allocates and frees: `sweeps` timed sweeps after 3
+ * warm-up sweeps each, CUDA events on stream.  Never changes the model (tile
+ * size, N, seed): every candidate gives bit-identical results.  *tuned =
+ * params with the fastest geometry filled in (fields already non-zero in
+ * params are kept fixed); *us_per_sweep (nullable) = its time.  Results are
+ * cached per device and (L, N, surfaces, tile, phase order, fixed fields):
+ * a repeated call returns at once.  Jobs that do not use the persistent
+ * engine are returned unchanged.  Synchronises the stream.  RSOS_EINVAL for
+ * invalid params or sweeps < 1, RSOS_ENOMEM / RSOS_ECUDA as rsos_init. */
+int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_params* tuned, double* us_per_sweep,
+                  void* stream);
 
 /* Create a job at time t = 0 with the flat initial condition (section II).
  *   dev_buf/dev_bytes  NULL/0: the library allocates and later frees the device

@@ -24,7 +24,7 @@ __all__ = [
     "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc", "rsos_advance",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "rsos_set_moments", "rsos_moments",
-    "rsos_read_moments", "library_path",
+    "rsos_read_moments", "rsos_autotune", "library_path",
 ]
 
 RSOS_OK = 0
@@ -54,11 +54,15 @@ class rsos_params(ctypes.Structure):
     """Mirror of the C struct rsos_params (include/rsos.h)."""
     _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("surfaces", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("phase_order", ctypes.c_int32),
-                ("series_capacity", ctypes.c_int32), ("engine", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("series_capacity", ctypes.c_int32), ("engine", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("words_per_thread", ctypes.c_int32), ("tiles_per_lane", ctypes.c_int32),
+                ("phase_lag", ctypes.c_int32)]
 
-    def __init__(self, L=64, N=1, surfaces=1, tile=8, phase_order=0, series_capacity=0, engine=0, seed=0):
+    def __init__(self, L=64, N=1, surfaces=1, tile=8, phase_order=0, series_capacity=0, engine=0, seed=0,
+                 words_per_thread=0, tiles_per_lane=0, phase_lag=0):
         super().__init__(int(L), int(N), int(surfaces), int(tile), int(tile), int(phase_order),
-                         int(series_capacity), int(engine), int(seed) & 0xFFFFFFFFFFFFFFFF)
+                         int(series_capacity), int(engine), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                         int(words_per_thread), int(tiles_per_lane), int(phase_lag))
 
 
 def library_path() -> str:
@@ -85,6 +89,7 @@ def _load():
             "rsos_read_series": [vp, P(i64), P(i64), P(i64), P(ctypes.c_double), i32, P(i32), vp],
             "rsos_heights": [vp, i32, P(i64), vp],
             "rsos_set_moments": [vp, i32],
+            "rsos_autotune": [P(rsos_params), i32, P(rsos_params), P(ctypes.c_double), vp],
             "rsos_moments": [vp, P(i64), P(i64), vp],
             "rsos_read_moments": [vp, P(i64), P(i64), P(ctypes.c_int8), i32, P(i32), vp],
             "rsos_time": [vp, P(i64)],
@@ -200,6 +205,16 @@ def _int128_rows(words: np.ndarray) -> list:
     flat = words.reshape(-1, 8)
     out = [[int(r[2 * k]) % (1 << 64) + (int(r[2 * k + 1]) << 64) for k in range(4)] for r in flat]
     return np.array(out, dtype=object).reshape(words.shape[:-1] + (4,))
+
+
+def rsos_autotune(params: rsos_params, sweeps: int = 20, stream=None):
+    """Fastest execution geometry for params' job shape (cached per device and
+    shape): (tuned rsos_params, microseconds per sweep)."""
+    tuned = rsos_params()
+    us = ctypes.c_double()
+    _check(_load().rsos_autotune(ctypes.byref(params), int(sweeps), ctypes.byref(tuned), ctypes.byref(us),
+                                 _stream(stream)), "rsos_autotune")
+    return tuned, us.value
 
 
 def rsos_set_moments(h, on: bool = True) -> None:

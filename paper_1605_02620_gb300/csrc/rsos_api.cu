@@ -10,7 +10,10 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rsos.h"
@@ -69,12 +72,13 @@ struct Layout {
 };
 
 // Tiles per lane and work item of the persistent engine (execution geometry
-// only): by default an item is 64 tiles (2 per lane with one thread per
-// tile, 4 with two), the fastest measured for L = 4096 and 64 surfaces on
-// GB300 at N = 1 and N = 2, and at most 8 per lane for wider jobs;
-// RSOS_TILES_PER_LANE overrides it.
-int persist_tiles_per_lane(int NWP)
+// only): params->tiles_per_lane if set, else RSOS_TILES_PER_LANE, else an
+// item of 64 tiles (2 per lane with one thread per tile, 4 with two), the
+// fastest measured for L = 4096 and 64 surfaces on GB300 at N = 1 and
+// N = 2, and at most 8 per lane for wider jobs.
+int persist_tiles_per_lane(const rsos_params* p, int NWP)
 {
+    if (p->tiles_per_lane > 0) return p->tiles_per_lane;
     if (const char* env = std::getenv("RSOS_TILES_PER_LANE")) {
         const int v = std::atoi(env);
         if (v >= 1 && v <= 64) return v;
@@ -84,10 +88,10 @@ int persist_tiles_per_lane(int NWP)
 
 // Tiles per work item: one warp's 32 lanes over the lane-word groups of a
 // tile, times the tiles per lane.
-int persist_block_tiles(int NWP)
+int persist_block_tiles(const rsos_params* p, int NWP)
 {
     const int cw = 32 / NWP;
-    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane(NWP);
+    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane(p, NWP);
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -97,14 +101,15 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // window is 1.5-2x larger, so fewer warps fit an SM; one word per thread was
 // measured faster there (L = 4096, 64 surfaces: 287 vs 305 us per sweep at
 // N = 2, 420 vs 499 at N = 4), unless it would need more than 32 threads per
-// tile.  RSOS_WORDS_PER_THREAD=1 forces one word per thread (execution
-// geometry only; results are identical).
-int words_per_thread(int NW, int N)
+// tile.  params->words_per_thread, else RSOS_WORDS_PER_THREAD=1, overrides
+// it (execution geometry only; results are identical).
+int words_per_thread(const rsos_params* p, int NW)
 {
+    if (p->words_per_thread == 1 || p->words_per_thread == 2) return p->words_per_thread;
     if (const char* env = std::getenv("RSOS_WORDS_PER_THREAD"))
         if (std::atoi(env) == 1) return 1;
     if (NW % 2 != 0) return 1;
-    if (rsos::bits_for_step(N) >= 3 && NW <= 32) return 1;
+    if (rsos::bits_for_step(p->N) >= 3 && NW <= 32) return 1;
     return 2;
 }
 
@@ -122,8 +127,13 @@ int validate(const rsos_params* p)
     if (p->series_capacity < 0 || p->series_capacity > (1 << 24)) return RSOS_EINVAL;
     if (p->engine < 0 || p->engine > 2) return RSOS_EINVAL;
     if (p->engine == 2 && p->surfaces == 1) return RSOS_EINVAL;  // plain path: phase engine only
+    const int NW = (p->surfaces + 31) / 32;
+    if (p->words_per_thread < 0 || p->words_per_thread > 2 || (p->words_per_thread == 2 && NW % 2 != 0))
+        return RSOS_EINVAL;
+    if (p->tiles_per_lane < 0 || p->tiles_per_lane > 64) return RSOS_EINVAL;
+    if (p->phase_lag < 0 || p->phase_lag == 1 || p->phase_lag > (1 << 20)) return RSOS_EINVAL;
     if (p->engine == 2) {
-        const int NW = (p->surfaces + 31) / 32, NWT = words_per_thread(NW, p->N);
+        const int NWT = words_per_thread(p, NW);
         if (NW / NWT > 32) return RSOS_EINVAL;
     }
     return RSOS_OK;
@@ -156,16 +166,14 @@ Layout layout_of(const rsos_params* p)
     l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && nT >= 8));
     if (l.persist_on && p->engine == 0) {
         // more lane-word groups than lanes of a warp: phase engine
-        const int NWT = words_per_thread(l.NW, p->N);
+        const int NWT = words_per_thread(p, l.NW);
         if (l.NW / NWT > 32) l.persist_on = false;
     }
     l.CW = l.K = 0;
     l.persist = 0;
     if (l.persist_on) {
-        const int NWT = words_per_thread(l.NW, p->N);
-        const int SX = l.T / 2;
-        (void)SX;
-        l.CW = persist_block_tiles(l.NW / NWT);
+        const int NWT = words_per_thread(p, l.NW);
+        l.CW = persist_block_tiles(p, l.NW / NWT);
         l.K = (nT + l.CW - 1) / l.CW;
         l.persist = align256((size_t)4 * nT * 8) + 256;
     }
@@ -380,13 +388,14 @@ cudaError_t launch_multi(int N, int SX, int words_per_thread, const MultiArgs& M
     }
 }
 
-cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out)
+cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, int phase_lag,
+                         PersistPlan* out)
 {
     switch (SX) {
-        case 1: return plan_persist_s1(J, words_per_thread, block_tiles, out);
-        case 2: return plan_persist_s2(J, words_per_thread, block_tiles, out);
-        case 4: return plan_persist_s4(J, words_per_thread, block_tiles, out);
-        case 8: return plan_persist_s8(J, words_per_thread, block_tiles, out);
+        case 1: return plan_persist_s1(J, words_per_thread, block_tiles, phase_lag, out);
+        case 2: return plan_persist_s2(J, words_per_thread, block_tiles, phase_lag, out);
+        case 4: return plan_persist_s4(J, words_per_thread, block_tiles, phase_lag, out);
+        case 8: return plan_persist_s8(J, words_per_thread, block_tiles, phase_lag, out);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -420,7 +429,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->SX = l.T / 2;
     h->B = l.B;
     h->NW = l.NW;
-    h->NWT = words_per_thread(l.NW, params->N);
+    h->NWT = words_per_thread(params, l.NW);
     h->S_pad = l.S_pad;
     h->cap = l.cap;
     h->ncb = l.ncb;
@@ -489,7 +498,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     J.rk = rsos::philox_round_keys(J.seed_lo, J.seed_hi);
     cudaError_t e = cudaSuccess;
     if (l.persist_on) {
-        e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, &h->plan);
+        e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, params->phase_lag, &h->plan);
         if (e == cudaSuccess && (h->plan.CW != l.CW || h->plan.K != l.K)) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) e = rsos::launch_zero(h->done, (size_t)4 * J.nT * 8, as_stream(stream));
         if (e == cudaSuccess) e = rsos::launch_zero(h->ticket, 16, as_stream(stream));
@@ -1028,7 +1037,7 @@ int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n
         if (t_max[i] < 0 || t_max[i] > kMaxSweeps) return RSOS_EINVAL;
         if (ps[i].surfaces > 1 && ps[i].engine == 0) {
             const int NW = (ps[i].surfaces + 31) / 32;
-            if (NW / words_per_thread(NW, ps[i].N) <= 32) ps[i].engine = 2;
+            if (NW / words_per_thread(&ps[i], NW) <= 32) ps[i].engine = 2;
         }
         size_t bytes = 0;
         const int rc = rsos_required_bytes(&ps[i], &bytes);
@@ -1197,3 +1206,124 @@ int rsos_batch_free(rsos_batch* b)
 }
 
 }  // extern "C"
+
+// ---- Autotuner of the execution geometry --------------------------------
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<rsos_params, double>> g_tune_cache;
+
+// Microseconds per sweep of one geometry on a scratch job: 3 warm-up
+// sweeps, then `sweeps` sweeps between CUDA events.
+int time_geometry(const rsos_params& p, int sweeps, cudaStream_t s, double* us)
+{
+    rsos_handle* h = nullptr;
+    int rc = rsos_init(&p, nullptr, 0, s, &h);
+    if (rc) return rc;
+    rc = rsos_sweep(h, 3, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (!rc && e == cudaSuccess) rc = rsos_sweep(h, sweeps, s);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const int rc_free = rsos_free(h);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RSOS_ECUDA;
+    }
+    if (rc_free) return rc_free;
+    *us = 1e3 * (double)ms / sweeps;
+    return RSOS_OK;
+}
+
+}  // namespace
+
+extern "C" int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_params* tuned, double* us_per_sweep,
+                             void* stream)
+{
+    if (!params || !tuned || sweeps < 1) return RSOS_EINVAL;
+    int rc = validate(params);
+    if (rc) return rc;
+    *tuned = *params;
+    if (us_per_sweep) *us_per_sweep = 0.0;
+    const Layout l = layout_of(params);
+    if (!l.persist_on) return RSOS_OK;  // nothing to choose outside the persistent engine
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RSOS_ECUDA;
+    }
+    const TuneKey key{dev, params->L, params->N, params->surfaces, l.T, params->phase_order,
+                      params->words_per_thread, params->tiles_per_lane, params->phase_lag};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *tuned = it->second.first;
+            tuned->seed = params->seed;
+            tuned->series_capacity = params->series_capacity;
+            if (us_per_sweep) *us_per_sweep = it->second.second;
+            return RSOS_OK;
+        }
+    }
+    // Candidates: words per thread {1, 2}, work items of 32 / 64 / 128 tiles,
+    // the automatic phase lag and a shorter one; fields set by the caller stay.
+    std::vector<int> wpts, tpls_items, lags;
+    if (params->words_per_thread) wpts = {params->words_per_thread};
+    else {
+        wpts = {1};
+        if (l.NW % 2 == 0) wpts.push_back(2);
+    }
+    const int nT = params->L / l.T;
+    if (params->phase_lag) lags = {params->phase_lag};
+    else {
+        lags = {0};
+        if (nT / 6 >= 2) lags.push_back(nT / 6);
+    }
+    cudaStream_t s = as_stream(stream);
+    rsos_params best = *params;
+    double best_us = -1.0;
+    for (int wpt : wpts) {
+        const int NWP = l.NW / wpt;
+        if (NWP > 32) continue;
+        const int lanes_per_tile_group = std::max(1, 32 / NWP);
+        std::vector<int> tpls;
+        if (params->tiles_per_lane) tpls = {params->tiles_per_lane};
+        else
+            for (int item : {32, 64, 128}) {
+                const int v = std::max(1, item / lanes_per_tile_group);
+                if (std::find(tpls.begin(), tpls.end(), v) == tpls.end() && v <= 64) tpls.push_back(v);
+            }
+        for (int tpl : tpls)
+            for (int lag : lags) {
+                rsos_params c = *params;
+                c.words_per_thread = wpt;
+                c.tiles_per_lane = tpl;
+                c.phase_lag = lag;
+                c.series_capacity = 1;
+                if (validate(&c) != RSOS_OK || !layout_of(&c).persist_on) continue;
+                double us = 0.0;
+                rc = time_geometry(c, sweeps, s, &us);
+                if (rc) return rc;
+                if (best_us < 0.0 || us < best_us) {
+                    best_us = us;
+                    best = c;
+                }
+            }
+    }
+    best.seed = params->seed;
+    best.series_capacity = params->series_capacity;
+    *tuned = best;
+    if (us_per_sweep) *us_per_sweep = best_us;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {best, best_us};
+    return RSOS_OK;
+}

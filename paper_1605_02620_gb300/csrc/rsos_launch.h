@@ -35,7 +35,9 @@ struct PersistPlan {
     int CW, K, D, nthr, grid;
     size_t smem;
 };
-cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, PersistPlan* out);
+// phase_lag >= 2 fixes the lag; 0 lets the plan choose it.
+cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, int phase_lag,
+                         PersistPlan* out);
 cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A,
                            const PersistPlan& P, cudaStream_t s);
 // Multi-job launch: all jobs share N, word width and SX.  grid from
@@ -54,7 +56,7 @@ RSOS_DECLARE_MULTI(8)
 #undef RSOS_DECLARE_MULTI
 
 #define RSOS_DECLARE_PERSIST(SX)                                                                      \
-    cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles,             \
+    cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles, int phase_lag, \
                                    PersistPlan* out);                                                  \
     cudaError_t launch_persist_s##SX(const JobDev& J, int words_per_thread, const PersistArgs& A,      \
                                      const PersistPlan& P, cudaStream_t s);

@@ -8,7 +8,7 @@
 namespace rsos {
 
 template <int N, typename WT, int SX>
-cudaError_t plan_persist_t(const JobDev& J, int block_tiles, PersistPlan* P)
+cudaError_t plan_persist_t(const JobDev& J, int block_tiles, int phase_lag, PersistPlan* P)
 {
     constexpr int B = bits_for_step(N);
     constexpr int WPB = PersistCfg<N, WT, SX>::WPB;
@@ -47,6 +47,7 @@ cudaError_t plan_persist_t(const JobDev& J, int block_tiles, PersistPlan* P)
         const int v = atoi(env);
         if (v >= 2) D = v;
     }
+    if (phase_lag >= 2) D = phase_lag;
     P->D = D;
     return cudaSuccess;
 }
@@ -103,10 +104,10 @@ cudaError_t launch_multi_t(const MultiArgs& M, int grid, int block, size_t smem,
     }
 
 template <int SX>
-cudaError_t plan_persist_sx(const JobDev& J, int words_per_thread, int block_tiles, PersistPlan* out)
+cudaError_t plan_persist_sx(const JobDev& J, int words_per_thread, int block_tiles, int phase_lag, PersistPlan* out)
 {
-#define RSOS_P64(NN) plan_persist_t<NN, uint64_t, SX>(J, block_tiles, out)
-#define RSOS_P32(NN) plan_persist_t<NN, uint32_t, SX>(J, block_tiles, out)
+#define RSOS_P64(NN) plan_persist_t<NN, uint64_t, SX>(J, block_tiles, phase_lag, out)
+#define RSOS_P32(NN) plan_persist_t<NN, uint32_t, SX>(J, block_tiles, phase_lag, out)
     RSOS_PERSIST_SWITCH(RSOS_P64, RSOS_P32)
 #undef RSOS_P64
 #undef RSOS_P32
@@ -160,10 +161,10 @@ cudaError_t launch_multi_sx(int N, int words_per_thread, const MultiArgs& M, int
 
 #define RSOS_DEFINE_PERSIST(SX)                                                                       \
     namespace rsos {                                                                                  \
-    cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles,             \
+    cudaError_t plan_persist_s##SX(const JobDev& J, int words_per_thread, int block_tiles, int phase_lag, \
                                    PersistPlan* out)                                                  \
     {                                                                                                 \
-        return plan_persist_sx<SX>(J, words_per_thread, block_tiles, out);                            \
+        return plan_persist_sx<SX>(J, words_per_thread, block_tiles, phase_lag, out);                 \
     }                                                                                                 \
     cudaError_t launch_persist_s##SX(const JobDev& J, int words_per_thread, const PersistArgs& A,     \
                                      const PersistPlan& P, cudaStream_t s)                            \

@@ -86,15 +86,22 @@ class Server:
     """hbm_budget: device bytes the resident jobs may hold.  epoch_s: target
     GPU time of one epoch (short epochs admit new work sooner)."""
 
-    def __init__(self, hbm_budget: int, epoch_s: float = 0.02, stream=None, rate_guess: float = 4e12):
+    def __init__(self, hbm_budget: int, epoch_s: float = 0.02, stream=None, rate_guess: float = 4e12,
+                 tune: bool = False):
         self.hbm_budget = int(hbm_budget)
         self.epoch_s = float(epoch_s)
         self.stream = stream
         self.rate = float(rate_guess)  # attempts/s estimate, refined every epoch
+        self.tune = bool(tune)  # execution geometry per job shape from rsos_autotune (cached)
 
-    @staticmethod
-    def _params(r: Request) -> rsos_params:
-        return rsos_params(L=r.L, N=r.N, surfaces=r.surfaces, tile=8, seed=r.seed, series_capacity=2)
+    def _params(self, r: Request) -> rsos_params:
+        p = rsos_params(L=r.L, N=r.N, surfaces=r.surfaces, tile=8, seed=r.seed, series_capacity=2)
+        if self.tune:
+            from . import rsos_autotune
+            tuned, _ = rsos_autotune(p, sweeps=10, stream=self.stream)
+            p.words_per_thread, p.tiles_per_lane, p.phase_lag = (tuned.words_per_thread, tuned.tiles_per_lane,
+                                                                 tuned.phase_lag)
+        return p
 
     def run(self, requests, clock=time.perf_counter, sleep=time.sleep) -> Report:
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))

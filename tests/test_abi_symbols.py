@@ -43,3 +43,17 @@ def test_invalid_params_rejected_without_gpu():
         with pytest.raises(R.RsosError):
             R.rsos_required_bytes(bad)
     assert R.rsos_required_bytes(R.rsos_params(L=4096, N=1, surfaces=64)) >= 2 * 4096 * 4096 * 8
+
+
+def test_execution_geometry_fields_validated_without_gpu():
+    import paper_1605_02620_gb300 as R
+    import pytest
+    for bad in [dict(surfaces=32, words_per_thread=2),  # one lane word cannot be split in two
+                dict(surfaces=64, words_per_thread=3), dict(surfaces=64, tiles_per_lane=65),
+                dict(surfaces=64, tiles_per_lane=-1), dict(surfaces=64, phase_lag=1),
+                dict(surfaces=64, phase_lag=-2)]:
+        with pytest.raises(R.RsosError):
+            R.rsos_required_bytes(R.rsos_params(L=256, N=1, **bad))
+    for good in [dict(surfaces=64, words_per_thread=1), dict(surfaces=64, words_per_thread=2),
+                 dict(surfaces=64, tiles_per_lane=4, phase_lag=12), dict(surfaces=96, words_per_thread=1)]:
+        assert R.rsos_required_bytes(R.rsos_params(L=256, N=1, **good)) > 0
