@@ -170,6 +170,21 @@ int rsos_moments(rsos_handle* h, int64_t* sums, int64_t* t_out, void* stream);
 int rsos_read_moments(rsos_handle* h, int64_t* times, int64_t* sums, int8_t* has, int32_t cap, int32_t* n_out,
                       void* stream);
 
+/* Checkpoint / resume (no counterpart in the paper).  With counter-based
+ * Philox a job's whole state is its parameters, t, the coded lattice (or the
+ * heights of the plain path), h(0,0) per surface, the measurement schedule
+ * and the measured series; a restored job continues bit-identically.
+ * rsos_snapshot_bytes: size of the snapshot of h in bytes.
+ * rsos_snapshot: write it into host_buf (caller-owned, >= that size;
+ *   RSOS_ENOMEM if smaller); synchronises the stream.
+ * rsos_restore: a new handle from a snapshot, like rsos_init (dev_buf /
+ *   dev_bytes as there); RSOS_EINVAL if the bytes are not a snapshot of this
+ *   format (checked before any device work).  Synchronises the stream. */
+int rsos_snapshot_bytes(const rsos_handle* h, size_t* bytes);
+int rsos_snapshot(rsos_handle* h, void* host_buf, size_t bytes, void* stream);
+int rsos_restore(const void* host_buf, size_t bytes, void* dev_buf, size_t dev_bytes, void* stream,
+                 rsos_handle** out);
+
 /* Absolute heights of one surface at the current time into host_LxL
  * (row-major, x fastest, int64 [L*L]).  Synchronises the stream. */
 int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream);

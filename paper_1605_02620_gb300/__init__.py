@@ -24,7 +24,8 @@ __all__ = [
     "rsos_selftest_timeout", "rsos_launches", "rsos_width_noalloc", "rsos_advance",
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "rsos_set_moments", "rsos_moments",
-    "rsos_read_moments", "rsos_autotune", "library_path",
+    "rsos_read_moments", "rsos_autotune", "rsos_snapshot", "rsos_restore", "rsos_snapshot_bytes",
+    "library_path",
 ]
 
 RSOS_OK = 0
@@ -89,6 +90,9 @@ def _load():
             "rsos_read_series": [vp, P(i64), P(i64), P(i64), P(ctypes.c_double), i32, P(i32), vp],
             "rsos_heights": [vp, i32, P(i64), vp],
             "rsos_set_moments": [vp, i32],
+            "rsos_snapshot_bytes": [vp, P(sz)],
+            "rsos_snapshot": [vp, vp, sz, vp],
+            "rsos_restore": [vp, sz, vp, sz, vp, P(vp)],
             "rsos_autotune": [P(rsos_params), i32, P(rsos_params), P(ctypes.c_double), vp],
             "rsos_moments": [vp, P(i64), P(i64), vp],
             "rsos_read_moments": [vp, P(i64), P(i64), P(ctypes.c_int8), i32, P(i32), vp],
@@ -215,6 +219,30 @@ def rsos_autotune(params: rsos_params, sweeps: int = 20, stream=None):
     _check(_load().rsos_autotune(ctypes.byref(params), int(sweeps), ctypes.byref(tuned), ctypes.byref(us),
                                  _stream(stream)), "rsos_autotune")
     return tuned, us.value
+
+
+def rsos_snapshot_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(_load().rsos_snapshot_bytes(h, ctypes.byref(n)), "rsos_snapshot_bytes")
+    return n.value
+
+
+def rsos_snapshot(h, stream=None) -> bytes:
+    """The job's whole state as bytes (bit-exact resume with rsos_restore)."""
+    n = ctypes.c_size_t()
+    _check(_load().rsos_snapshot_bytes(h, ctypes.byref(n)), "rsos_snapshot_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_load().rsos_snapshot(h, buf, n.value, _stream(stream)), "rsos_snapshot")
+    return buf.raw
+
+
+def rsos_restore(data: bytes, dev_buf: int = 0, dev_bytes: int = 0, stream=None):
+    """A new handle continuing the snapshot's job."""
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(_load().rsos_restore(buf, len(data), ctypes.c_void_p(dev_buf or None), int(dev_bytes),
+                                _stream(stream), ctypes.byref(h)), "rsos_restore")
+    return h
 
 
 def rsos_set_moments(h, on: bool = True) -> None:

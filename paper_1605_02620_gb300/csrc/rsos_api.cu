@@ -1327,3 +1327,157 @@ extern "C" int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_par
     g_tune_cache[key] = {best, best_us};
     return RSOS_OK;
 }
+
+// ---- Checkpoint / resume -----------------------------------------------
+// A snapshot is a host byte string: a fixed header, the schedule and series
+// times, then the device state (coded lattice or heights, h00, measured
+// series rows).  With counter-based Philox that is the whole state of a job:
+// a restored job continues bit-identically.
+namespace {
+
+constexpr char kSnapMagic[8] = {'R', 'S', 'O', 'S', 'S', 'N', 'P', '1'};
+
+struct SnapHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    rsos_params params;
+    int64_t t;
+    int32_t moments;
+    int32_t n_series;
+    int32_t n_sched;
+    int32_t sched_pos;
+    uint64_t lattice_bytes;
+    uint64_t h00_bytes;
+    uint64_t series_bytes;
+};
+
+size_t pad8(size_t v) { return (v + 7) & ~(size_t)7; }
+
+size_t lattice_bytes_of(const rsos_handle* h)
+{
+    const size_t L = (size_t)h->p.L;
+    return h->plain ? L * L * 4 : (size_t)h->B * L * L * h->NW * 4;
+}
+
+size_t snapshot_size(const rsos_handle* h)
+{
+    const size_t n = h->series_t.size();
+    return sizeof(SnapHeader) + 8 * h->sched.size() + 8 * n + pad8(n) + pad8(lattice_bytes_of(h)) +
+           (size_t)h->S_pad * 8 + n * (size_t)h->S_pad * kRecWords * 8;
+}
+
+}  // namespace
+
+extern "C" int rsos_snapshot_bytes(const rsos_handle* h, size_t* bytes)
+{
+    if (!h || !bytes) return RSOS_EINVAL;
+    *bytes = snapshot_size(h);
+    return RSOS_OK;
+}
+
+extern "C" int rsos_snapshot(rsos_handle* h, void* host_buf, size_t bytes, void* stream)
+{
+    if (!h || !host_buf) return RSOS_EINVAL;
+    if (h->sticky) return h->sticky;
+    if (bytes < snapshot_size(h)) return RSOS_ENOMEM;
+    cudaStream_t s = as_stream(stream);
+    int rc = check_device_error(h, s);
+    if (rc) return rc;
+    unsigned char* out = static_cast<unsigned char*>(host_buf);
+    SnapHeader hd{};
+    std::memcpy(hd.magic, kSnapMagic, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof(SnapHeader);
+    hd.params = h->p;
+    hd.t = h->t;
+    hd.moments = h->moments ? 1 : 0;
+    hd.n_series = (int32_t)h->series_t.size();
+    hd.n_sched = (int32_t)h->sched.size();
+    hd.sched_pos = (int32_t)h->sched_pos;
+    hd.lattice_bytes = lattice_bytes_of(h);
+    hd.h00_bytes = (uint64_t)h->S_pad * 8;
+    hd.series_bytes = (uint64_t)hd.n_series * h->S_pad * kRecWords * 8;
+    size_t off = 0;
+    std::memcpy(out, &hd, sizeof(hd));
+    off += sizeof(hd);
+    std::memcpy(out + off, h->sched.data(), 8 * h->sched.size());
+    off += 8 * h->sched.size();
+    std::memcpy(out + off, h->series_t.data(), 8 * h->series_t.size());
+    off += 8 * h->series_t.size();
+    std::memset(out + off, 0, pad8(h->series_mom.size()));
+    if (!h->series_mom.empty()) std::memcpy(out + off, h->series_mom.data(), h->series_mom.size());
+    off += pad8(h->series_mom.size());
+    const void* lattice = h->plain ? (const void*)h->J.heights : (const void*)h->J.planes;
+    cudaError_t e = cudaMemcpyAsync(out + off, lattice, hd.lattice_bytes, cudaMemcpyDeviceToHost, s);
+    off += pad8(hd.lattice_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out + off, h->J.h00, hd.h00_bytes, cudaMemcpyDeviceToHost, s);
+    off += hd.h00_bytes;
+    if (e == cudaSuccess && hd.series_bytes)
+        e = cudaMemcpyAsync(out + off, h->rec, hd.series_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    return RSOS_OK;
+}
+
+extern "C" int rsos_restore(const void* host_buf, size_t bytes, void* dev_buf, size_t dev_bytes, void* stream,
+                            rsos_handle** out)
+{
+    if (!out) return RSOS_EINVAL;
+    *out = nullptr;
+    if (!host_buf || bytes < sizeof(SnapHeader)) return RSOS_EINVAL;
+    const unsigned char* in = static_cast<const unsigned char*>(host_buf);
+    SnapHeader hd;
+    std::memcpy(&hd, in, sizeof(hd));
+    if (std::memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(SnapHeader))
+        return RSOS_EINVAL;
+    if (validate(&hd.params) != RSOS_OK || hd.t < 0 || hd.t > kMaxSweeps || hd.n_series < 0 || hd.n_sched < 0 ||
+        hd.sched_pos < 0 || hd.sched_pos > hd.n_sched || (hd.moments != 0 && hd.moments != 1))
+        return RSOS_EINVAL;
+    const Layout l = layout_of(&hd.params);
+    const size_t L = (size_t)hd.params.L;
+    const size_t lattice = l.plain ? L * L * 4 : (size_t)l.B * L * L * l.NW * 4;
+    const size_t n = (size_t)hd.n_series;
+    if (hd.lattice_bytes != lattice || hd.h00_bytes != (size_t)l.S_pad * 8 || (int)n > l.cap ||
+        hd.series_bytes != n * l.S_pad * kRecWords * 8)
+        return RSOS_EINVAL;
+    const size_t need = sizeof(SnapHeader) + 8 * (size_t)hd.n_sched + 8 * n + pad8(n) + pad8(lattice) +
+                        hd.h00_bytes + hd.series_bytes;
+    if (bytes < need) return RSOS_EINVAL;
+    rsos_handle* h = nullptr;
+    int rc = rsos_init(&hd.params, dev_buf, dev_bytes, stream, &h);
+    if (rc) return rc;
+    size_t off = sizeof(SnapHeader);
+    h->sched.assign(reinterpret_cast<const int64_t*>(in + off), reinterpret_cast<const int64_t*>(in + off) + hd.n_sched);
+    off += 8 * (size_t)hd.n_sched;
+    h->sched_pos = (size_t)hd.sched_pos;
+    h->series_t.assign(reinterpret_cast<const int64_t*>(in + off), reinterpret_cast<const int64_t*>(in + off) + n);
+    off += 8 * n;
+    h->series_mom.assign(in + off, in + off + n);
+    off += pad8(n);
+    h->t = hd.t;
+    h->moments = hd.moments != 0;
+    cudaStream_t s = as_stream(stream);
+    void* lat = h->plain ? (void*)h->J.heights : (void*)h->J.planes;
+    cudaError_t e = cudaMemcpyAsync(lat, in + off, lattice, cudaMemcpyHostToDevice, s);
+    off += pad8(lattice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->J.h00, in + off, hd.h00_bytes, cudaMemcpyHostToDevice, s);
+    off += hd.h00_bytes;
+    if (e == cudaSuccess && hd.series_bytes)
+        e = cudaMemcpyAsync(h->rec, in + off, hd.series_bytes, cudaMemcpyHostToDevice, s);
+    // The persistent engine counts completed items per (phase, tile row) from
+    // t = 0: a job resumed at t has completed t sweeps of every row.
+    std::vector<unsigned long long> done;
+    if (e == cudaSuccess && h->persist) {
+        done.assign((size_t)4 * h->J.nT, (unsigned long long)hd.t * (unsigned long long)h->plan.K);
+        e = cudaMemcpyAsync(h->done, done.data(), done.size() * 8, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        rsos_free(h);
+        return RSOS_ECUDA;
+    }
+    *out = h;
+    return RSOS_OK;
+}

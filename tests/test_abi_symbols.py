@@ -57,3 +57,12 @@ def test_execution_geometry_fields_validated_without_gpu():
     for good in [dict(surfaces=64, words_per_thread=1), dict(surfaces=64, words_per_thread=2),
                  dict(surfaces=64, tiles_per_lane=4, phase_lag=12), dict(surfaces=96, words_per_thread=1)]:
         assert R.rsos_required_bytes(R.rsos_params(L=256, N=1, **good)) > 0
+
+
+def test_restore_rejects_foreign_bytes_without_gpu():
+    import paper_1605_02620_gb300 as R
+    import pytest
+    for junk in (b"", b"RSOSSNP1", b"not a snapshot" * 20, b"RSOSSNP1" + b"\x02\x00\x00\x00" + b"\x00" * 200):
+        with pytest.raises(R.RsosError) as e:
+            R.rsos_restore(junk)
+        assert e.value.status == -1  # RSOS_EINVAL, before any device call
