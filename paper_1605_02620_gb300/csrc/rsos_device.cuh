@@ -75,6 +75,45 @@ RSOS_HD size_t plane_word(const JobDev& J, size_t rec, int b, int w)
     return (rec * (size_t)J.B + (size_t)b) * (size_t)J.NW + (size_t)w;
 }
 
+// Word offsets (plane 0, lane word w0) of the window columns i = -1..SX and
+// rows j = -1..SY of the active sub-tile of tile (tx, ty) in the sweep's
+// tiling; plane b is b * NW words further.
+template <int SX>
+struct WindowIndex {
+    size_t col[SX + 2];
+    size_t row[SX + 2];
+};
+
+template <int SX>
+RSOS_HD void window_index(const JobDev& J, int tx, int ty, int qx, int qy, int ox,
+                                             int oy, int w0, WindowIndex<SX>& wi)
+{
+    constexpr int T = 2 * SX;  // square tiles: the tile edge is known at compile time
+    const int nT = J.nT, L = J.L;
+    const size_t rec_words = (size_t)J.B * J.NW;
+#pragma unroll
+    for (int ii = 0; ii < SX + 2; ++ii) {
+        int xr = ox + qx * SX + ii - 1;  // in [-1, 2T)
+        int dm = 0;
+        if (xr < 0) {
+            xr += T;
+            dm = -1;
+        } else if (xr >= T) {
+            xr -= T;
+            dm = 1;
+        }
+        int col = tx + dm;
+        col = col < 0 ? col + nT : (col >= nT ? col - nT : col);
+        wi.col[ii] = ((size_t)xr * nT + col) * rec_words + w0;
+    }
+#pragma unroll
+    for (int jj = 0; jj < SX + 2; ++jj) {
+        int y = oy + ty * T + qy * SX + jj - 1;  // in [-1, L + T)
+        y = y < 0 ? y + L : (y >= L ? y - L : y);
+        wi.row[jj] = (size_t)y * ((size_t)T * nT * rec_words);
+    }
+}
+
 #if defined(__CUDACC__)
 
 template <typename WT>
@@ -204,45 +243,6 @@ __device__ __forceinline__ void store_rec(WT* p, const WT (&v)[B])
     } else {
 #pragma unroll
         for (int b = 0; b < B; ++b) p[b] = v[b];
-    }
-}
-
-// Word offsets (plane 0, lane word w0) of the window columns i = -1..SX and
-// rows j = -1..SY of the active sub-tile of tile (tx, ty) in the sweep's
-// tiling; plane b is b * NW words further.
-template <int SX>
-struct WindowIndex {
-    size_t col[SX + 2];
-    size_t row[SX + 2];
-};
-
-template <int SX>
-__device__ __forceinline__ void window_index(const JobDev& J, int tx, int ty, int qx, int qy, int ox,
-                                             int oy, int w0, WindowIndex<SX>& wi)
-{
-    constexpr int T = 2 * SX;  // square tiles: the tile edge is known at compile time
-    const int nT = J.nT, L = J.L;
-    const size_t rec_words = (size_t)J.B * J.NW;
-#pragma unroll
-    for (int ii = 0; ii < SX + 2; ++ii) {
-        int xr = ox + qx * SX + ii - 1;  // in [-1, 2T)
-        int dm = 0;
-        if (xr < 0) {
-            xr += T;
-            dm = -1;
-        } else if (xr >= T) {
-            xr -= T;
-            dm = 1;
-        }
-        int col = tx + dm;
-        col = col < 0 ? col + nT : (col >= nT ? col - nT : col);
-        wi.col[ii] = ((size_t)xr * nT + col) * rec_words + w0;
-    }
-#pragma unroll
-    for (int jj = 0; jj < SX + 2; ++jj) {
-        int y = oy + ty * T + qy * SX + jj - 1;  // in [-1, L + T)
-        y = y < 0 ? y + L : (y >= L ? y - L : y);
-        wi.row[jj] = (size_t)y * ((size_t)T * nT * rec_words);
     }
 }
 

@@ -113,3 +113,60 @@ int probe_deps(const int* g8, const int* item4, int64_t* out12)
     return n;
 }
 }
+
+// Window address arithmetic of the sweep kernels (window_index) against the
+// plain definition: slot (jj, ii) of the active sub-tile q of tile (tx, ty)
+// holds site ((ox + tx T + qx SX + ii - 1) mod L, (oy + ty T + qy SX + jj - 1)
+// mod L), whose plane-b word of lane word w is (((y T + x mod T) nT + x div T)
+// B + b) NW + w.  Every combination of origin, set, tile, lane-word group,
+// non-corner slot and plane is checked; returns the number of mismatches or
+// out-of-range offsets and the number of checks in *n_checked.
+template <int SX>
+static long long window_check(int L, int NW, int B, int NWT, long long* n_checked)
+{
+    constexpr int T = 2 * SX;
+    rsos::JobDev J{};
+    J.L = L;
+    J.T = T;
+    J.nT = L / T;
+    J.NW = NW;
+    J.B = B;
+    const long long total = (long long)B * L * L * NW;
+    long long bad = 0, n = 0;
+    for (int oy = 0; oy < T; ++oy)
+        for (int ox = 0; ox < T; ++ox)
+            for (int q = 0; q < 4; ++q)
+                for (int ty = 0; ty < J.nT; ++ty)
+                    for (int tx = 0; tx < J.nT; ++tx)
+                        for (int w0 = 0; w0 + NWT <= NW; w0 += NWT) {
+                            rsos::WindowIndex<SX> wi;
+                            rsos::window_index<SX>(J, tx, ty, q & 1, q >> 1, ox, oy, w0, wi);
+                            for (int jj = 0; jj < SX + 2; ++jj)
+                                for (int ii = 0; ii < SX + 2; ++ii) {
+                                    if ((jj == 0 || jj == SX + 1) && (ii == 0 || ii == SX + 1)) continue;
+                                    const int x = ((ox + tx * T + (q & 1) * SX + ii - 1) % L + L) % L;
+                                    const int y = ((oy + ty * T + (q >> 1) * SX + jj - 1) % L + L) % L;
+                                    const long long rec = ((long long)y * T + x % T) * J.nT + x / T;
+                                    for (int b = 0; b < B; ++b)
+                                        for (int w = 0; w < NWT; ++w) {
+                                            const long long want = (rec * B + b) * NW + w0 + w;
+                                            const long long got = (long long)(wi.row[jj] + wi.col[ii]) + (long long)b * NW + w;
+                                            bad += (got != want || got < 0 || got >= total) ? 1 : 0;
+                                            ++n;
+                                        }
+                                }
+                        }
+    *n_checked = n;
+    return bad;
+}
+
+extern "C" long long probe_window_check(int L, int T, int NW, int B, int NWT, long long* n_checked)
+{
+    switch (T) {
+        case 2: return window_check<1>(L, NW, B, NWT, n_checked);
+        case 4: return window_check<2>(L, NW, B, NWT, n_checked);
+        case 8: return window_check<4>(L, NW, B, NWT, n_checked);
+        case 16: return window_check<8>(L, NW, B, NWT, n_checked);
+        default: return -1;
+    }
+}

@@ -104,3 +104,16 @@ def test_origin_site_location(probe):
                 x = (ox + tx * T + qx * S + k % S) % L
                 y = (oy + ty * T + qy * S + k // S) % L
                 assert (x, y) == (0, 0)
+
+
+@pytest.mark.parametrize("L,T", [(16, 2), (16, 4), (32, 8), (64, 16), (24, 8), (8, 8), (16, 8), (48, 16)])
+@pytest.mark.parametrize("NW,B,NWT", [(1, 2, 1), (2, 2, 2), (2, 3, 1), (3, 4, 1), (4, 3, 2)])
+def test_window_addresses_in_bounds_and_exact(probe, L, T, NW, B, NWT):
+    """Every word the sweep kernels stage or write back, for every tiling
+    origin, sub-tile set, tile and lane-word group, is inside the lattice and
+    is the intended site's word (including the periodic wraps)."""
+    probe.probe_window_check.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_longlong)]
+    probe.probe_window_check.restype = ctypes.c_longlong
+    n = ctypes.c_longlong()
+    bad = probe.probe_window_check(L, T, NW, B, NWT, ctypes.byref(n))
+    assert bad == 0 and n.value > 0
