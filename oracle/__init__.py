@@ -58,6 +58,8 @@ def _load():
             lib.orc_philox_bulk.restype = None
             lib.orc_control.argtypes = [ctypes.c_void_p, ctypes.c_uint64, i32p, i32p, i32p]
             lib.orc_control.restype = None
+            lib.orc_axis_half.argtypes = [ctypes.c_int32] * 4 + [i32p, i32p]
+            lib.orc_axis_half.restype = None
             lib.orc_sweeps.argtypes = [ctypes.c_void_p, i64p, u32p, ctypes.c_int32, ctypes.c_uint64,
                                        ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, i64p]
             lib.orc_sweeps.restype = ctypes.c_int
@@ -73,7 +75,7 @@ def _load():
 
 class _Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("Tx", ctypes.c_int32),
-                ("Ty", ctypes.c_int32), ("phase_order", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("Ty", ctypes.c_int32), ("phase_order", ctypes.c_int32), ("tiling", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -81,16 +83,19 @@ class _Params(ctypes.Structure):
 class Params:
     """Model parameters: lattice edge L, step bound N (Eq. 6), DT tile Tx x Ty
     (section II; 8 x 8 in the paper's runs), phase order (0: random per sweep,
-    1: fixed 0,1,2,3) and the Philox key."""
+    1: fixed 0,1,2,3), the Philox key, and the tiling: 0 for regular tiles
+    (Tx, Ty even, dividing L), 1 for the (+1) tilings of section III.C (tiles
+    Tx or Tx + 1 wide, Ty or Ty + 1 high)."""
     L: int
     N: int
     Tx: int = 8
     Ty: int = 8
     phase_order: int = 0
     seed: int = 0
+    tiling: int = 0
 
     def c(self) -> _Params:
-        return _Params(self.L, self.N, self.Tx, self.Ty, self.phase_order, 0,
+        return _Params(self.L, self.N, self.Tx, self.Ty, self.phase_order, self.tiling,
                        self.seed & 0xFFFFFFFFFFFFFFFF)
 
 
@@ -135,6 +140,15 @@ def control(p: Params, t: int):
     pc = p.c()
     lib.orc_control(ctypes.byref(pc), t, ctypes.byref(ox), ctypes.byref(oy), _ptr(perm, ctypes.c_int32))
     return ox.value, oy.value, tuple(int(v) for v in perm)
+
+
+def axis_half(L: int, T: int, c: int, half: int):
+    """(start, width) in pattern coordinates of half `half` of tile c along an
+    axis of a (+1) tiling with base edge T (section III.C)."""
+    lib = _load()
+    a, w = ctypes.c_int32(), ctypes.c_int32()
+    lib.orc_axis_half(L, T, c, half, ctypes.byref(a), ctypes.byref(w))
+    return a.value, w.value
 
 
 def flat(L: int, n_lanes: int) -> np.ndarray:

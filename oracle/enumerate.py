@@ -20,6 +20,11 @@ site x; keep the configuration if Eq. 6 rejects it"):
   a = (Tx/2)(Ty/2) sites receives 2a selections, each of a uniformly chosen
   site of the sub-tile, acted on with probability 1/2 (the random half mask).
   One selection is the kernel  1/2 I + 1/(2a) sum_{k in sub-tile} A_k.
+* DT on a (+1) tiling (section III.C): tiles T or T + 1 wide (the first
+  L mod T of the L div T tiles of an axis are the wider ones), each halved
+  into floor(w/2) and w - floor(w/2) sites; the origin is uniform over one
+  period of the pattern (T if T divides L, else L) and a sub-tile of a sites
+  receives 2a selections with the kernel above for its own a.
 
 From the stationary distribution pi of each chain we get the growth velocity
 v (mean height gain per site per sweep / Monte-Carlo step) and the stationary
@@ -187,5 +192,75 @@ def dt_chain(L: int, N: int, Tx: int, Ty: int, phase_order: int = 0,
     pi = _power(lambda d: run(d, False)[0], d0, tol, max_iter)
     _, reward = run(pi, True)
     return {"L": L, "N": N, "Tx": Tx, "Ty": Ty, "phase_order": phase_order,
+            "n_states": len(states), "velocity": reward / (L * L),
+            "w2": float(pi @ width2_of_states(states))}
+
+
+def _halves(L: int, T: int):
+    """Per tile of one axis of a (+1) tiling: the two halves as (start,
+    width) in pattern coordinates."""
+    n, r = L // T, L % T
+    assert 1 <= n and r <= n
+    out, x = [], 0
+    for c in range(n):
+        w = T + 1 if c < r else T
+        out.append(((x, w // 2), (x + w // 2, w - w // 2)))
+        x += w
+    assert x == L
+    return out
+
+
+def _dt_sequences_general(L: int, Tx: int, Ty: int, phase_order: int):
+    hx, hy = _halves(L, Tx), _halves(L, Ty)
+    px = Tx if L % Tx == 0 else L
+    py = Ty if L % Ty == 0 else L
+    perms = [tuple(range(4))] if phase_order == 1 else list(itertools.permutations(range(4)))
+    seqs = []
+    for oy in range(py):
+        for ox in range(px):
+            for perm in perms:
+                phases = []
+                for q in perm:
+                    qx, qy = q & 1, q >> 1
+                    subtiles = []
+                    for (ys, yw) in (h[qy] for h in hy):
+                        for (xs, xw) in (h[qx] for h in hx):
+                            subtiles.append([((oy + ys + j) % L) * L + (ox + xs + i) % L
+                                             for j in range(yw) for i in range(xw)])
+                    phases.append(subtiles)
+                seqs.append(phases)
+    return seqs
+
+
+def dt_chain_general(L: int, N: int, Tx: int, Ty: int, phase_order: int = 0,
+                     tol: float = 1e-14, max_iter: int = 100000):
+    """Stationary DT growth velocity (per site per sweep) and E[W^2] on a (+1)
+    tiling (section III.C)."""
+    states, index = enumerate_states(L, N)
+    target, accepted = attempt_maps(L, N, states, index)
+    seqs = _dt_sequences_general(L, Tx, Ty, phase_order)
+
+    def run(d, with_reward):
+        total = np.zeros_like(d)
+        reward = 0.0
+        for phases in seqs:
+            e = d.copy()
+            for subtiles in phases:
+                for sites in subtiles:
+                    a = len(sites)
+                    for _ in range(2 * a):
+                        nxt = 0.5 * e
+                        for k in sites:
+                            if with_reward:
+                                reward += float(e @ accepted[k]) / (2 * a) / len(seqs)
+                            nxt += _push(e, target[k]) / (2 * a)
+                        e = nxt
+            total += e / len(seqs)
+        return total, reward
+
+    d0 = np.full(len(states), 1.0 / len(states))
+    pi = _power(lambda d: run(d, False)[0], d0, tol, max_iter)
+    _, reward = run(pi, True)
+    return {"L": L, "N": N, "Tx": Tx, "Ty": Ty, "phase_order": phase_order, "tiling": 1,
             "n_states": len(states), "velocity": reward / (L * L),
             "w2": float(pi @ width2_of_states(states))}

@@ -15,7 +15,8 @@
  *   - double tiling (DT) domain decomposition (section II): the lattice is cut
  *     into Tx x Ty tiles, each tile into 2 x 2 sub-tiles, giving four sets of
  *     sub-tiles that are updated one set after another; the tiling origin is
- *     moved randomly after every sweep;
+ *     moved randomly after every sweep; and the irregular (+1) tilings of the
+ *     decomposition check (section III.C), whose tiles are T or T + 1 wide;
  *   - multisurface coding (section II): the surfaces ("lanes") of one job share
  *     the sequence of selected sites; each lane takes part in a selection only
  *     if its own random mask bit is set ("updating only half of the selected
@@ -114,22 +115,32 @@ static void orc_permutation(uint32_t index, int perm[4])
 typedef struct {
     int32_t L;           /* periodic lattice edge                              */
     int32_t N;           /* step bound of Eq. 6                                */
-    int32_t Tx, Ty;      /* DT tile edges (even), L % Tx == 0 and L % Ty == 0  */
+    int32_t Tx, Ty;      /* DT tile edges: even and dividing L (tiling 0), or  */
+                         /* the base edges of a (+1) tiling (tiling 1)         */
     int32_t phase_order; /* 0: random permutation per sweep, 1: fixed 0,1,2,3  */
-    int32_t pad_;
+    int32_t tiling;      /* 0: regular Tx x Ty tiles, 1: Tx(+1) x Ty(+1) tiles  */
     uint64_t seed;       /* Philox key                                         */
 } orc_params;
 
-/* Control draw of sweep t: origin of the tiling and order of the four
- * sub-tile sets (section II: "the origin of the DD was moved randomly"). */
+/* Period of the tiling pattern along an axis of edge T: T when the tiles
+ * are all T wide, else the whole lattice (a (+1) tiling repeats only
+ * after L sites). */
+static int32_t orc_period(const orc_params* P, int32_t T)
+{
+    return (P->tiling == 1 && P->L % T != 0) ? P->L : T;
+}
+
+/* Control draw of sweep t: origin of the tiling, uniform over one period of
+ * the pattern, and order of the four sub-tile sets (section II: the origin
+ * of the decomposition moves randomly after every sweep). */
 void orc_control(const orc_params* P, uint64_t t, int32_t* ox, int32_t* oy, int32_t perm[4])
 {
     uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
     uint32_t ctr[4] = {0u, (uint32_t)t, 0u, 1u << 30};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
-    *ox = (int32_t)orc_mulhi32(r[0], (uint32_t)P->Tx);
-    *oy = (int32_t)orc_mulhi32(r[1], (uint32_t)P->Ty);
+    *ox = (int32_t)orc_mulhi32(r[0], (uint32_t)orc_period(P, P->Tx));
+    *oy = (int32_t)orc_mulhi32(r[1], (uint32_t)orc_period(P, P->Ty));
     if (P->phase_order == 1) {
         for (int m = 0; m < 4; ++m) perm[m] = m;
     } else {
@@ -203,6 +214,84 @@ static int64_t orc_dt_sweep_lane(const orc_params* P, int64_t* h, uint32_t lane,
     return accepted;
 }
 
+/*
+ * (+1) tilings (section III.C: domains of 6(+1) x 10(+1) sites).  When T does
+ * not divide L, the L sites of an axis are cut into n = L div T tiles of which
+ * the first r = L mod T are one site wider, so the widths add up to L (this
+ * needs r <= n).  In pattern coordinates tile c starts at c T + min(c, r).
+ * Every tile is halved: the first half has floor(w/2) sites, the second the
+ * other w - floor(w/2), so sub-tiles of one set are always separated by a
+ * half of the other set.  With T even and dividing L this is the regular
+ * tiling above.
+ */
+typedef struct {
+    int32_t T, n, r;
+} orc_axis;
+
+static orc_axis orc_axis_of(int32_t L, int32_t T)
+{
+    orc_axis a = {T, L / T, L % T};
+    return a;
+}
+
+/* Start (pattern coordinate) and width of half `half` of tile c. */
+void orc_axis_half(int32_t L, int32_t T, int32_t c, int32_t half, int32_t* start, int32_t* width)
+{
+    const orc_axis a = orc_axis_of(L, T);
+    const int32_t X = c * a.T + (c < a.r ? c : a.r);
+    const int32_t w = a.T + (c < a.r ? 1 : 0);
+    const int32_t w0 = w / 2;
+    *start = X + (half ? w0 : 0);
+    *width = half ? w - w0 : w0;
+}
+
+/* One DT sweep of a single lane on a (+1) tiling: as orc_dt_sweep_lane, with
+ * the sub-tile of tile (tx, ty) in set q spanning the halves above, a its
+ * area and 2a selections per activation. */
+static int64_t orc_dt_sweep_lane_general(const orc_params* P, int64_t* h, uint32_t lane, uint64_t t)
+{
+    const int32_t L = P->L;
+    const orc_axis ax = orc_axis_of(L, P->Tx), ay = orc_axis_of(L, P->Ty);
+    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    int32_t ox, oy, perm[4];
+    int64_t accepted = 0;
+    orc_control(P, t, &ox, &oy, perm);
+    for (int p = 0; p < 4; ++p) {
+        const int q = perm[p];
+        const int32_t qx = q & 1, qy = q >> 1;
+        for (int32_t ty = 0; ty < ay.n; ++ty) {
+            for (int32_t tx = 0; tx < ax.n; ++tx) {
+                const uint32_t tile_id = (uint32_t)(ty * ax.n + tx);
+                int32_t u0, sx, v0, sy;
+                orc_axis_half(L, P->Tx, tx, qx, &u0, &sx);
+                orc_axis_half(L, P->Ty, ty, qy, &v0, &sy);
+                const uint32_t a = (uint32_t)(sx * sy);
+                uint32_t site_r[4], mask_r[4];
+                for (uint32_t i = 0; i < 2u * a; ++i) {
+                    if ((i & 7u) == 0) {
+                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 3, (2u << 30) | ((uint32_t)p << 28)};
+                        orc_philox4x32_10(c, key, site_r);
+                    }
+                    if ((i & 3u) == 0) {
+                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 2,
+                                         (3u << 30) | ((uint32_t)p << 28) | (lane >> 5)};
+                        orc_philox4x32_10(c, key, mask_r);
+                    }
+                    uint32_t word = site_r[(i >> 1) & 3u];
+                    uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
+                    uint32_t k = (half * a) >> 16;
+                    uint32_t bit = (mask_r[i & 3u] >> (lane & 31u)) & 1u;
+                    if (!bit) continue;
+                    int32_t x = (ox + u0 + (int32_t)(k % (uint32_t)sx)) % L;
+                    int32_t y = (oy + v0 + (int32_t)(k / (uint32_t)sx)) % L;
+                    accepted += orc_attempt(h, L, P->N, x, y);
+                }
+            }
+        }
+    }
+    return accepted;
+}
+
 /* One random-sequential Monte-Carlo step (L^2 attempts) of a single lane. */
 static int64_t orc_rs_step_lane(const orc_params* P, int64_t* h, uint32_t lane, uint64_t s)
 {
@@ -234,9 +323,14 @@ int orc_sweeps(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n
                uint64_t t0, uint64_t n_sweeps, int32_t rs, int32_t n_threads, int64_t* accepted)
 {
     if (P->L < 1 || P->N < 1 || n_lanes < 0) return -1;
-    if (!rs) {
+    if (P->tiling != 0 && P->tiling != 1) return -1;
+    if (!rs && P->tiling == 0) {
         if (P->Tx < 2 || P->Ty < 2 || (P->Tx & 1) || (P->Ty & 1)) return -1;
         if (P->L % P->Tx || P->L % P->Ty) return -1;
+    }
+    if (!rs && P->tiling == 1) {
+        if (P->Tx < 2 || P->Ty < 2 || P->Tx > 256 || P->Ty > 256 || P->L < P->Tx || P->L < P->Ty) return -1;
+        if (P->L % P->Tx > P->L / P->Tx || P->L % P->Ty > P->L / P->Ty) return -1;
     }
     const int64_t area = (int64_t)P->L * P->L;
     if (n_threads < 1) n_threads = 1;
@@ -245,7 +339,8 @@ int orc_sweeps(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n
         int64_t acc = 0;
         for (uint64_t t = t0; t < t0 + n_sweeps; ++t) {
             acc += rs ? orc_rs_step_lane(P, h + m * area, lanes[m], t)
-                      : orc_dt_sweep_lane(P, h + m * area, lanes[m], t);
+                      : P->tiling == 1 ? orc_dt_sweep_lane_general(P, h + m * area, lanes[m], t)
+                                       : orc_dt_sweep_lane(P, h + m * area, lanes[m], t);
         }
         if (accepted) accepted[m] = acc;
     }
