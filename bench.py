@@ -32,31 +32,43 @@ sys.path.insert(0, ROOT)
 METRIC = "RSOS site-update attempts/s on 1 GB300 (plain vs batched); % HBM roofline"
 WORKLOAD = dict(workload="ms-n1: L=4096 periodic, N=1, 64 surfaces bit-sliced in uint64 words, 8x8 DT tiles, "
                          "flat start, 1e4 sweeps, W^2 per surface at 40 log-spaced times",
-                L=4096, N=1, surfaces=64, tile=8, sweeps=10000, measurements=40)
-KERNEL_SOURCES = ["paper_1605_02620_gb300/csrc/rsos_device.cuh", "paper_1605_02620_gb300/csrc/rsos_persist.cuh",
-                  "paper_1605_02620_gb300/csrc/rsos_sched.cuh", "paper_1605_02620_gb300/csrc/rsos_logic.cuh",
-                  "paper_1605_02620_gb300/csrc/philox.cuh", "paper_1605_02620_gb300/csrc/rsos_persist_launch.cuh"]
-PROFILE = os.path.join(ROOT, "profiles", "persistent_kernel_L4096_N1_S64.md")
+                L=4096, N=1, surfaces=64, tile=8, tiling=0, sweeps=10000, measurements=40)
+# The (+1) tilings of the decomposition check (section III.C) on the paper's
+# largest lattice, which no regular tile divides (9605 = 5 x 17 x 113).
+WORKLOAD_IRREGULAR = dict(workload="ms-irregular: L=9605 periodic, N=1, 64 surfaces bit-sliced in uint64 words, "
+                                   "6(+1)x10(+1) DT tiles, flat start, 2000 sweeps, W^2 per surface at 30 "
+                                   "log-spaced times",
+                          L=9605, N=1, surfaces=64, tile=(6, 10), tiling=1, sweeps=2000, measurements=30)
+CSRC = "paper_1605_02620_gb300/csrc/"
+KERNELS = {
+    0: dict(name="rsos::persistent_kernel<1, uint64_t, 4>", launches_per_sweep=None,
+            profile="persistent_kernel_L4096_N1_S64.md",
+            sources=["rsos_device.cuh", "rsos_persist.cuh", "rsos_sched.cuh", "rsos_logic.cuh", "philox.cuh",
+                     "rsos_persist_launch.cuh"]),
+    1: dict(name="rsos::general_phase_kernel<1, uint64_t>", launches_per_sweep=4,
+            profile="general_phase_kernel_L9605_N1_S64.md",
+            sources=["rsos_device.cuh", "rsos_general.cu", "rsos_general.cuh", "rsos_logic.cuh", "philox.cuh"]),
+}
 
 
-def kernel_hash() -> str:
+def kernel_hash(tiling: int = 0) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
+    for rel in KERNELS[tiling]["sources"]:
+        with open(os.path.join(ROOT, CSRC + rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(tiling: int = 0):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     try:
-        text = open(PROFILE).read()
+        text = open(os.path.join(ROOT, "profiles", KERNELS[tiling]["profile"])).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_hash():
+    if not m or not t or m.group(1) != kernel_hash(tiling):
         return None
     return float(t.group(1))
 
@@ -165,7 +177,7 @@ def run_gpu(args):
     times = log_schedule(sweeps, W["measurements"])
     seed = rank
     params = R.rsos_params(L=L, N=W["N"], surfaces=S, tile=W["tile"], seed=seed,
-                           series_capacity=len(times) + 1)
+                           series_capacity=len(times) + 1, tiling=W["tiling"])
     nbytes = R.rsos_required_bytes(params)
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     base = (buf.data_ptr() + 255) // 256 * 256
@@ -204,7 +216,8 @@ def run_gpu(args):
         return
 
     # Dominant kernel, timed alone on the same stream: one persistent launch
-    # of n_kernel_sweeps sweeps (no measurement inside).
+    # of n_kernel_sweeps sweeps (no measurement inside), or, on a (+1)
+    # tiling, the 4 n_kernel_sweeps phase launches of as many sweeps.
     h = R.rsos_init(params, dev_buf=base, dev_bytes=nbytes, stream=stream)
     R.rsos_sweep(h, 50, stream=stream)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -223,7 +236,8 @@ def run_gpu(args):
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        p2 = R.rsos_params(L=L, N=W["N"], surfaces=S, tile=W["tile"], seed=seed, series_capacity=len(times) + 1)
+        p2 = R.rsos_params(L=L, N=W["N"], surfaces=S, tile=W["tile"], seed=seed, series_capacity=len(times) + 1,
+                           tiling=W["tiling"])
         h = R.rsos_init(p2, stream=stream)
         R.rsos_schedule(h, times)
         R.rsos_sweep(h, sweeps, stream=stream)
@@ -236,24 +250,29 @@ def run_gpu(args):
     value = aggregate_rate(attempts, world, args.steps, dev_ms)
     e2e_value = aggregate_rate(attempts, world, e2e_steps, e2e_s * 1e3)
     peaks, peak_src = measured_peaks()
-    alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S * n_kernel_sweeps  # per launch
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    K = KERNELS[W["tiling"]]
+    # launches in the kernel-timing region: one persistent launch, or four
+    # phase launches per sweep
+    n_launch = K["launches_per_sweep"] * n_kernel_sweeps if K["launches_per_sweep"] else 1
+    alg_bytes = 2.0 * (rsos_bits(W["N"]) / 8.0) * L * L * S * n_kernel_sweeps / n_launch  # per launch
+    per_launch_ms = launch_ms / n_launch
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     launches_per_job = launches[0]
     if rank != 0:
         return
-    cpu = cpu_baseline(L, W["N"], W["tile"], seed) if world == 1 else None
+    cpu = cpu_baseline(L, W["N"], W["tile"], seed, tiling=W["tiling"]) if world == 1 else None
+    lanes_note = f"inputs larger than L2 ({L * L * S * rsos_bits(W['N']) / 8 / 2 ** 20:.0f} MiB lattice per job)"
     line = {
         "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 (bit-sliced int)", "data": "synthetic",
-        "config": dict(W, parallelism=f"replicas{world}", l2="inputs larger than L2 (256 MiB lattice per job)",
-                       seed=seed),
+        "config": dict(W, parallelism=f"replicas{world}", l2=lanes_note, seed=seed),
         "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": (len(times)) * S * 4 * 8 + 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
-                     "kernel": "rsos::persistent_kernel<1, uint64_t, 4>", "launch_ms": launch_ms,
-                     "sweeps_per_launch": n_kernel_sweeps,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(W["tiling"]),
+                     "kernel": K["name"], "launch_ms": per_launch_ms,
+                     "sweeps_per_launch": n_kernel_sweeps / n_launch,
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -267,13 +286,18 @@ def rsos_bits(N: int) -> int:
     return 2 if N <= 1 else (3 if N <= 3 else 4)
 
 
-def cpu_baseline(L, N, T, seed, target_s: float = 12.0):
-    """The oracle, as it stands, on the host cores: one DT sweep of L = 4096 for
-    as many lanes as there are cores (one lane per thread), repeated until
-    about ``target_s`` seconds of CPU work."""
+def _edges(T):
+    return (T, T) if not isinstance(T, (tuple, list)) else tuple(T)
+
+
+def cpu_baseline(L, N, T, seed, target_s: float = 12.0, tiling: int = 0):
+    """The oracle, as it stands, on the host cores: one DT sweep of the
+    workload's lattice for as many lanes as there are cores (one lane per
+    thread), repeated until about ``target_s`` seconds of CPU work."""
     import oracle as O
     cores = os.cpu_count() or 1
-    p = O.Params(L=L, N=N, Tx=T, Ty=T, seed=seed)
+    Tx, Ty = _edges(T)
+    p = O.Params(L=L, N=N, Tx=Tx, Ty=Ty, seed=seed, tiling=tiling)
     lanes = list(range(cores))
     h = O.flat(L, cores)
     done, t0 = 0, time.perf_counter()
@@ -429,7 +453,8 @@ def run_reference(args):
     W = WORKLOAD
     cores = os.cpu_count() or 1
     L = W["L"]
-    p = O.Params(L=L, N=W["N"], Tx=W["tile"], Ty=W["tile"], seed=0)
+    Tx, Ty = _edges(W["tile"])
+    p = O.Params(L=L, N=W["N"], Tx=Tx, Ty=Ty, seed=0, tiling=W["tiling"])
     lanes = list(range(cores))
     h = O.flat(L, cores)
     for k in range(args.warmup):
@@ -460,7 +485,7 @@ def main():
                     help="sweeps per job (reduced values only for profiling captures)")
     ap.add_argument("--measurements", type=int, default=WORKLOAD["measurements"],
                     help="measurement times per job (reduced values only for profiling captures)")
-    ap.add_argument("--workload", default="ms-n1", choices=["ms-n1", "batched", "served"])
+    ap.add_argument("--workload", default="ms-n1", choices=["ms-n1", "irregular", "batched", "served"])
     ap.add_argument("--batch-scale", type=int, default=1,
                     help="divide the batched jobs' t_max by this factor (profiling / quick checks)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
@@ -471,6 +496,13 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="profiling capture: timed steps only (no kernel timing, e2e or CPU baseline)")
     args = ap.parse_args()
+    if args.workload == "irregular":
+        WORKLOAD.clear()
+        WORKLOAD.update(WORKLOAD_IRREGULAR)
+        if "--sweeps" not in sys.argv:
+            args.sweeps = WORKLOAD["sweeps"]
+        if "--measurements" not in sys.argv:
+            args.measurements = WORKLOAD["measurements"]
     if args.sweeps != WORKLOAD["sweeps"] or args.measurements != WORKLOAD["measurements"]:
         WORKLOAD["sweeps"] = args.sweeps
         WORKLOAD["measurements"] = max(2, min(args.measurements, args.sweeps))

@@ -59,9 +59,11 @@ typedef struct rsos_batch rsos_batch;
  *                the stream); S > 1 the multisurface path with ceil(S/32)
  *                32-lane words per site and bit plane.  Lane j of any job is the
  *                same surface whatever S is.
- *   tile_x/y     DT tile edges (section II; 8 x 8 in the paper); the GPU path
- *                supports square tiles 2, 4, 8 and 16.  Part of the model: they
- *                change the dynamics.  0 means 8.
+ *   tile_x/y     DT tile edges (section II; 8 x 8 in the paper).  With
+ *                tiling 0 the tiles are square, 2, 4, 8 or 16, dividing L;
+ *                with tiling 1 they are the base edges Tx, Ty (2..30 each) of
+ *                a (+1) tiling.  Part of the model: they change the
+ *                dynamics.  0 means 8.
  *   phase_order  0: random permutation of the four sub-tile sets each sweep;
  *                1: fixed order 0,1,2,3.
  *   series_capacity  number of measurements the device series buffer holds
@@ -76,7 +78,17 @@ typedef struct rsos_batch rsos_batch;
  *                an even number of words).
  *   tiles_per_lane  tiles a lane runs per work item, 1..64.
  *   phase_lag    slots between consecutive phase fronts of the ticket order,
- *                >= 2.                                                        */
+ *                >= 2.
+ *   tiling       0: regular tiles (above).  1: the (+1) tilings of the
+ *                decomposition check (section III.C: 6(+1) x 10(+1)): along
+ *                each axis the first L mod T of the L div T tiles are one
+ *                site wider (needs L mod T <= L div T), every tile is halved
+ *                into floor(w/2) and the rest, and the per-sweep origin is
+ *                uniform over one period of the pattern (T if T divides L,
+ *                else L).  With T even and dividing L it is the regular
+ *                tiling, bit for bit.  Multisurface jobs (surfaces >= 2) on
+ *                the one-launch-per-phase engine (engine 0 or 1) only; the
+ *                lattice is stored with site records in row-major order.   */
 typedef struct {
     int32_t L;
     int32_t N;
@@ -90,6 +102,7 @@ typedef struct {
     int32_t words_per_thread;
     int32_t tiles_per_lane;
     int32_t phase_lag;
+    int32_t tiling;
 } rsos_params;
 
 /* Bytes of device memory a job needs (lattice planes, h(0,0) per surface,

@@ -57,13 +57,17 @@ class rsos_params(ctypes.Structure):
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("phase_order", ctypes.c_int32),
                 ("series_capacity", ctypes.c_int32), ("engine", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("words_per_thread", ctypes.c_int32), ("tiles_per_lane", ctypes.c_int32),
-                ("phase_lag", ctypes.c_int32)]
+                ("phase_lag", ctypes.c_int32), ("tiling", ctypes.c_int32)]
 
     def __init__(self, L=64, N=1, surfaces=1, tile=8, phase_order=0, series_capacity=0, engine=0, seed=0,
-                 words_per_thread=0, tiles_per_lane=0, phase_lag=0):
-        super().__init__(int(L), int(N), int(surfaces), int(tile), int(tile), int(phase_order),
+                 words_per_thread=0, tiles_per_lane=0, phase_lag=0, tiling=0, tile_y=None):
+        # tile: square edge, or (Tx, Ty); tile_y overrides the second edge
+        tx, ty = (tile, tile) if not isinstance(tile, (tuple, list)) else tile
+        if tile_y is not None:
+            ty = tile_y
+        super().__init__(int(L), int(N), int(surfaces), int(tx), int(ty), int(phase_order),
                          int(series_capacity), int(engine), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                         int(words_per_thread), int(tiles_per_lane), int(phase_lag))
+                         int(words_per_thread), int(tiles_per_lane), int(phase_lag), int(tiling))
 
 
 def library_path() -> str:

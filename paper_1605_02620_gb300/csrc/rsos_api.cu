@@ -26,6 +26,8 @@ struct rsos_handle {
     bool plain;
     int SX, B, NW, NWT, S_pad;
     JobDev J;
+    bool general;        // (+1) tiling of section III.C
+    rsos::GenTiling G;   // its geometry (general only)
     unsigned char* base;
     size_t bytes;
     bool owns;
@@ -118,9 +120,26 @@ int validate(const rsos_params* p)
     if (!p) return RSOS_EINVAL;
     const int T = p->tile_x == 0 ? 8 : p->tile_x;
     const int Ty = p->tile_y == 0 ? 8 : p->tile_y;
-    if (T != Ty) return RSOS_EINVAL;
-    if (T != 2 && T != 4 && T != 8 && T != 16) return RSOS_EINVAL;
-    if (p->L < T || p->L > 65536 || p->L % T != 0) return RSOS_EINVAL;
+    if (p->tiling == 1) {
+        // (+1) tilings: multisurface jobs on the phase engine; halves of at
+        // most 16 sites (the kernel's k / w by multiplication), and a window
+        // of 32 threads within one block's shared memory.
+        if (T > 30 || Ty > 30 || p->L > 65536) return RSOS_EINVAL;
+        if (!rsos::gen_axis_valid(p->L, T) || !rsos::gen_axis_valid(p->L, Ty)) return RSOS_EINVAL;
+        if (p->surfaces < 2 || p->engine == 2) return RSOS_EINVAL;
+        if (p->N < 1 || p->N > 7 || p->surfaces > (1 << 20)) return RSOS_EINVAL;
+        if (p->words_per_thread < 0 || p->words_per_thread > 2) return RSOS_EINVAL;
+        const rsos::GenTiling G = rsos::gen_tiling(p->L, T, Ty);
+        const int NWc = (p->surfaces + 31) / 32;
+        const size_t per_thread = (size_t)(G.max_w + 2) * (G.max_h + 2) * rsos::bits_for_step(p->N) * 4 *
+                                  (size_t)words_per_thread(p, NWc);
+        if (per_thread * 32 > 200 * 1024) return RSOS_EINVAL;
+    } else {
+        if (p->tiling != 0) return RSOS_EINVAL;
+        if (T != Ty) return RSOS_EINVAL;
+        if (T != 2 && T != 4 && T != 8 && T != 16) return RSOS_EINVAL;
+        if (p->L < T || p->L > 65536 || p->L % T != 0) return RSOS_EINVAL;
+    }
     if (p->N < 1 || p->N > 7) return RSOS_EINVAL;
     if (p->surfaces < 1 || p->surfaces > (1 << 20)) return RSOS_EINVAL;
     if (p->phase_order != 0 && p->phase_order != 1) return RSOS_EINVAL;
@@ -142,7 +161,9 @@ int validate(const rsos_params* p)
 Layout layout_of(const rsos_params* p)
 {
     Layout l;
-    l.T = p->tile_x == 0 ? 8 : p->tile_x;
+    // Layout tile edge: the class interleaving of the regular tiling, or
+    // row-major site records (edge 1) for the (+1) tilings.
+    l.T = p->tiling == 1 ? 1 : (p->tile_x == 0 ? 8 : p->tile_x);
     l.plain = p->surfaces == 1;
     l.B = rsos::bits_for_step(p->N);
     l.NW = (p->surfaces + 31) / 32;
@@ -163,7 +184,7 @@ Layout layout_of(const rsos_params* p)
     const int nT = p->L / l.T;
     // Auto engine: the persistent dataflow engine for multisurface jobs with
     // at least 8 tile rows, one launch per phase otherwise.
-    l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && nT >= 8));
+    l.persist_on = !l.plain && p->tiling == 0 && (p->engine == 2 || (p->engine == 0 && nT >= 8));
     if (l.persist_on && p->engine == 0) {
         // more lane-word groups than lanes of a warp: phase engine
         const int NWT = words_per_thread(p, l.NW);
@@ -234,8 +255,29 @@ int measure_due(rsos_handle* h, cudaStream_t s)
     return RSOS_OK;
 }
 
+// One sweep on a (+1) tiling: the control draw over one period of the
+// pattern, then one launch per phase.
+int run_sweep_general(rsos_handle* h, cudaStream_t s)
+{
+    const uint32_t t = (uint32_t)h->t;
+    const int L = h->J.L;
+    const rsos::Control c =
+        rsos::sweep_control(h->J.seed_lo, h->J.seed_hi, t, rsos::gen_period(L, h->p.tile_x),
+                            rsos::gen_period(L, h->p.tile_y), h->p.phase_order);
+    const rsos::GenOrigin o = rsos::gen_locate_origin_site(L, h->G, c.ox, c.oy);
+    for (int p = 0; p < 4; ++p) {
+        const cudaError_t e =
+            rsos::launch_phase_general(h->J, h->G, h->NWT, t, p, c.perm[p], c.ox, c.oy, o, h->smem_budget, s);
+        if (e != cudaSuccess) return fail_cuda(h, e);
+        h->launches += 1;
+    }
+    h->t += 1;
+    return RSOS_OK;
+}
+
 int run_sweep(rsos_handle* h, cudaStream_t s)
 {
+    if (h->general) return run_sweep_general(h, s);
     const uint32_t t = (uint32_t)h->t;
     const rsos::Control c = rsos::sweep_control(h->J.seed_lo, h->J.seed_hi, t, h->J.T, h->J.T,
                                                 h->p.phase_order);
@@ -424,7 +466,14 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     rsos_handle* h = new (std::nothrow) rsos_handle();
     if (!h) return RSOS_ENOMEM;
     h->p = *params;
-    h->p.tile_x = h->p.tile_y = l.T;
+    h->general = params->tiling == 1;
+    if (h->general) {
+        h->p.tile_x = params->tile_x == 0 ? 8 : params->tile_x;
+        h->p.tile_y = params->tile_y == 0 ? 8 : params->tile_y;
+        h->G = rsos::gen_tiling(params->L, h->p.tile_x, h->p.tile_y);
+    } else {
+        h->p.tile_x = h->p.tile_y = l.T;
+    }
     h->plain = l.plain;
     h->SX = l.T / 2;
     h->B = l.B;

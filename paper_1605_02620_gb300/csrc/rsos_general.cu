@@ -1,0 +1,174 @@
+// Phase kernel of the double-tiling sweep on the (+1) tilings of the
+// decomposition check (section III.C): one launch activates sub-tile set
+// q = perm[p] of every tile, one thread per (tile, lane-word group), as the
+// regular phase kernel does, with the tile and sub-tile extents taken at run
+// time (T or T + 1 wide tiles, halves of floor(w/2) and the rest).  Each
+// selection is Eq. 6 on bit-sliced words; the stream is the regular one with
+// a = the sub-tile's own area: 2a selections per activation, site index
+// k = floor(u a / 2^16) of a 16-bit u, kx = k mod w, ky = k div w.
+#include "rsos_general.cuh"
+#include "rsos_launch.h"
+
+namespace rsos {
+
+namespace {
+
+template <int N, typename WT, bool HAS00>
+__device__ __forceinline__ void general_activate(const JobDev& J, const GenTiling& G, WT* __restrict__ sm, int tid,
+                                                 int nthr, int tx, int ty, int wp, uint32_t t, int p, int q, int ox,
+                                                 int oy, int k00)
+{
+    constexpr int B = bits_for_step(N);
+    constexpr int NWT = (int)(sizeof(WT) / 4);
+    const int qx = q & 1, qy = q >> 1;
+    const int w0 = wp * NWT;
+    const int L = J.L;
+    int u0, sw, v0, sh;
+    gen_half(G.x, tx, qx, u0, sw);
+    gen_half(G.y, ty, qy, v0, sh);
+    const int WW = sw + 2;
+    const size_t rec_words = (size_t)B * J.NW;
+    const bool whole_record = NWT == J.NW;
+    const size_t rs = (size_t)nthr * B;  // one slot
+
+    // Stage the sub-tile and its one-site halo (corners unused).
+    for (int jj = 0; jj < sh + 2; ++jj) {
+        const bool edge_row = jj == 0 || jj == sh + 1;
+        for (int ii = edge_row ? 1 : 0; ii < (edge_row ? sw + 1 : sw + 2); ++ii) {
+            WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
+            stage_record_async<WT, B>(slot, J.planes + gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0),
+                                      J.NW, whole_record);
+        }
+    }
+    stage_wait_all();
+
+    const uint32_t tile_id = (uint32_t)(ty * G.x.n + tx);
+    const uint32_t A = (uint32_t)(sw * sh);
+    const int NSEL = 2 * (int)A;
+    const uint32_t inv = gen_inv((uint32_t)sw);
+    const uint32_t pbits = (uint32_t)p << 28;
+#pragma unroll 1
+    for (int g8 = 0; g8 < (NSEL + 7) / 8; ++g8) {
+        const U4 site_r = philox4x32_10(U4{tile_id, t, (uint32_t)g8, kDomSite | pbits}, J.rk);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int g = 2 * g8 + h;
+            if (4 * g >= NSEL) break;
+            const U4 m_lo = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0}, J.rk);
+            U4 m_hi = m_lo;
+            if (NWT == 2) m_hi = philox4x32_10(U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)}, J.rk);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i8 = 4 * h + r;
+                if (8 * g8 + i8 >= NSEL) break;
+                const uint32_t word = pick_word(site_r, i8 >> 1);
+                const uint32_t half = (i8 & 1) ? (word >> 16) : (word & 0xFFFFu);
+                const uint32_t k = (half * A) >> 16;
+                const uint32_t ky = gen_div(k, inv);
+                const uint32_t kx = k - ky * (uint32_t)sw;
+                const int s = ((int)ky + 1) * WW + (int)kx + 1;
+                WT* base = sm + ((size_t)s * nthr + tid) * B;
+                WT x[B], e[B], w[B], n[B], so[B];
+                load_rec<B, WT>(base, x);
+                load_rec<B, WT>(base + rs, e);
+                load_rec<B, WT>(base - rs, w);
+                load_rec<B, WT>(base - (size_t)WW * rs, n);
+                load_rec<B, WT>(base + (size_t)WW * rs, so);
+                const WT acc = accept_mask<N, B, WT>(mask_word<WT>(m_lo, m_hi, r), x, e, w, n, so);
+                masked_increment<B, WT>(x, acc);
+                store_rec<B, WT>(base, x);
+                if (HAS00 && (int)k == k00) record_origin_deposits<WT>(J.h00, w0 * 32, acc);
+            }
+        }
+    }
+
+    // Write the interior back.
+    for (int jj = 1; jj <= sh; ++jj) {
+        for (int ii = 1; ii <= sw; ++ii) {
+            const WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
+            uint32_t* dst = J.planes + gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0);
+            WT v[B];
+            load_rec<B, WT>(slot, v);
+            if (B * sizeof(WT) == 16 && whole_record) {
+                if (sizeof(WT) == 8)
+                    *reinterpret_cast<ulonglong2*>(dst) =
+                        make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
+                else
+                    *reinterpret_cast<uint4*>(dst) =
+                        make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) *reinterpret_cast<WT*>(dst + (size_t)b * J.NW) = v[b];
+            }
+        }
+    }
+}
+
+template <int N, typename WT>
+__global__ void __launch_bounds__(256) general_phase_kernel(JobDev J, GenTiling G, uint32_t t, int p, int q, int ox,
+                                                            int oy, GenOrigin o)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WT* sm = reinterpret_cast<WT*>(smem_raw);
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const long long gid = (long long)blockIdx.x * nthr + tid;
+    const long long per_row = (long long)G.x.n * J.NWP;
+    if (gid >= per_row * G.y.n) return;
+    const int ty = (int)(gid / per_row);
+    const int rem = (int)(gid - (long long)ty * per_row);
+    const int tx = rem / J.NWP, wp = rem - tx * J.NWP;
+    if (q == o.q && tx == o.tx && ty == o.ty)
+        general_activate<N, WT, true>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, o.k);
+    else
+        general_activate<N, WT, false>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, -1);
+}
+
+template <int N, typename WT>
+cudaError_t launch_general_t(const JobDev& J, const GenTiling& G, uint32_t t, int p, int q, int ox, int oy,
+                             const GenOrigin& o, size_t smem_budget, cudaStream_t s)
+{
+    constexpr int B = bits_for_step(N);
+    const size_t per_thread = (size_t)(G.max_w + 2) * (G.max_h + 2) * B * sizeof(WT);
+    const long long total = (long long)G.x.n * G.y.n * J.NWP;
+    long long n = (long long)(smem_budget / per_thread) / 32 * 32;
+    if (n > 256) n = 256;
+    if (n < 32) n = 32;
+    const size_t smem = per_thread * (size_t)n;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(general_phase_kernel<N, WT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const long long blocks = (total + n - 1) / n;
+    general_phase_kernel<N, WT><<<(unsigned)blocks, (unsigned)n, smem, s>>>(J, G, t, p, q, ox, oy, o);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_per_thread, uint32_t t, int p, int q,
+                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s)
+{
+#define RSOS_CASE(NN)                                                                             \
+    case NN:                                                                                      \
+        return words_per_thread == 2                                                              \
+                   ? launch_general_t<NN, uint64_t>(J, G, t, p, q, ox, oy, o, smem_budget, s)     \
+                   : launch_general_t<NN, uint32_t>(J, G, t, p, q, ox, oy, o, smem_budget, s);
+    switch (J.N) {
+        RSOS_CASE(1)
+        RSOS_CASE(2)
+        RSOS_CASE(3)
+        RSOS_CASE(4)
+        RSOS_CASE(5)
+        RSOS_CASE(6)
+        RSOS_CASE(7)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef RSOS_CASE
+}
+
+}  // namespace rsos

@@ -1,0 +1,138 @@
+// Geometry of the (+1) tilings of the decomposition check (section III.C:
+// domains of 6(+1) x 10(+1) sites).  Host and device.
+//
+// Along an axis of L sites and base edge T there are n = L div T tiles; the
+// first r = L mod T of them are one site wider, so the widths add up to L
+// (r <= n).  In pattern coordinates tile c starts at c T + min(c, r).  Every
+// tile is halved into floor(w/2) sites (half 0) and the rest (half 1); the
+// halves of one set are always separated by a half of the other set, so a set
+// can be updated in parallel (section II).  The pattern repeats after T sites
+// when T divides L, else after L: the per-sweep origin is uniform over that
+// period.  With T even and dividing L this is the regular tiling.
+//
+// Lattice layout for these tilings: site records in row-major order (record
+// index y L + x), the layout of the regular tiling with a tile edge of 1, so
+// the measurement kernels read it unchanged.
+#pragma once
+#include "rsos_common.cuh"
+
+namespace rsos {
+
+struct GenAxis {
+    int32_t T, n, r;
+};
+
+RSOS_HD GenAxis gen_axis(int L, int T)
+{
+    return GenAxis{T, L / T, L % T};
+}
+
+RSOS_HD bool gen_axis_valid(int L, int T)
+{
+    return T >= 2 && L >= T && L % T <= L / T;
+}
+
+RSOS_HD int gen_period(int L, int T)
+{
+    return L % T == 0 ? T : L;
+}
+
+// Start (pattern coordinate) and width of half `half` of tile c.
+RSOS_HD void gen_half(const GenAxis& a, int c, int half, int& start, int& width)
+{
+    const int X = c * a.T + (c < a.r ? c : a.r);
+    const int w = a.T + (c < a.r ? 1 : 0);
+    const int w0 = w >> 1;
+    start = X + (half ? w0 : 0);
+    width = half ? w - w0 : w0;
+}
+
+// Tile holding pattern coordinate u in [0, L).
+RSOS_HD int gen_tile_of(const GenAxis& a, int u)
+{
+    const int wide = a.r * (a.T + 1);
+    return u < wide ? u / (a.T + 1) : a.r + (u - wide) / a.T;
+}
+
+// Widest half of the axis (the window of a sub-tile is this plus a halo).
+RSOS_HD int gen_max_half(const GenAxis& a)
+{
+    return (a.T + (a.r > 0 ? 1 : 0) + 1) >> 1;
+}
+
+// v in [-L, 2L) -> v mod L.
+RSOS_HD int gen_wrap(int v, int L)
+{
+    return v < 0 ? v + L : (v >= L ? v - L : v);
+}
+
+// Word offset (plane 0, lane word w0) of window slot (ii, jj) of the
+// sub-tile whose first site is pattern coordinate (u0, v0): the record of
+// site ((ox + u0 + ii - 1) mod L, (oy + v0 + jj - 1) mod L) in row-major
+// order, rec_words words per record.  ii, jj = 0 and w + 1, h + 1 are the
+// halo.
+RSOS_HD size_t gen_window_word(int L, size_t rec_words, int ox, int oy, int u0, int v0, int ii, int jj, int w0)
+{
+    const size_t x = (size_t)gen_wrap(ox + u0 + ii - 1, L);
+    const size_t y = (size_t)gen_wrap(oy + v0 + jj - 1, L);
+    return (y * (size_t)L + x) * rec_words + (size_t)w0;
+}
+
+// floor(k / w) for k < 4096 and 1 <= w <= 16 by a multiply with
+// inv = ceil(2^16 / w): k inv / 2^16 exceeds k / w by k e / (w 2^16) with
+// e = inv w - 2^16 < w, which stays below 1 / w (the distance from k / w to
+// the next integer) while k e < 2^16.
+RSOS_HD uint32_t gen_inv(uint32_t w)
+{
+    return (65536u + w - 1u) / w;
+}
+
+RSOS_HD uint32_t gen_div(uint32_t k, uint32_t inv)
+{
+    return (k * inv) >> 16;
+}
+
+struct GenTiling {
+    GenAxis x, y;
+    int32_t max_w, max_h;  // widest half along x and y
+};
+
+RSOS_HD GenTiling gen_tiling(int L, int Tx, int Ty)
+{
+    GenTiling G;
+    G.x = gen_axis(L, Tx);
+    G.y = gen_axis(L, Ty);
+    G.max_w = gen_max_half(G.x);
+    G.max_h = gen_max_half(G.y);
+    return G;
+}
+
+// Where site (0,0) lies in the tiling of one sweep (origin ox, oy).
+struct GenOrigin {
+    int tx, ty;  // tile
+    int q;       // sub-tile set
+    int k;       // site index inside the sub-tile (row-major, k = ky w + kx)
+};
+
+RSOS_HD GenOrigin gen_locate_origin_site(int L, const GenTiling& G, int ox, int oy)
+{
+    const int u = ox == 0 ? 0 : L - ox, v = oy == 0 ? 0 : L - oy;
+    GenOrigin o;
+    o.tx = gen_tile_of(G.x, u);
+    o.ty = gen_tile_of(G.y, v);
+    int s0, w0, s1, w1;
+    gen_half(G.x, o.tx, 1, s1, w1);
+    (void)w1;
+    const int qx = u >= s1 ? 1 : 0;
+    gen_half(G.x, o.tx, qx, s0, w0);
+    int t0, h0, t1, h1;
+    gen_half(G.y, o.ty, 1, t1, h1);
+    (void)h1;
+    const int qy = v >= t1 ? 1 : 0;
+    gen_half(G.y, o.ty, qy, t0, h0);
+    o.q = 2 * qy + qx;
+    o.k = (v - t0) * w0 + (u - s0);
+    return o;
+}
+
+}  // namespace rsos

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "rsos_device.cuh"
+#include "rsos_general.cuh"
 #include "rsos_persist.cuh"
 
 namespace rsos {
@@ -15,6 +16,11 @@ cudaError_t launch_phase(const JobDev& J, int SX, int words_per_thread, uint32_t
                          int ox, int oy, const Origin00& o, size_t smem_budget, cudaStream_t s);
 cudaError_t launch_phase_plain(const JobDev& J, int SX, uint32_t t, int p, int q, int ox, int oy,
                                size_t smem_budget, cudaStream_t s);
+
+// One phase on a (+1) tiling (section III.C): sub-tile set q = perm[p] of
+// every tile of G; o locates site (0,0) in this sweep's tiling.
+cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_per_thread, uint32_t t, int p, int q,
+                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s);
 
 #define RSOS_DECLARE_SX(SX)                                                                          \
     cudaError_t launch_phase_s##SX(const JobDev& J, int words_per_thread, uint32_t t, int p, int q,  \

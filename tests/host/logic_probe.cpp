@@ -2,6 +2,9 @@
 // locate_origin_site) for CPU tests.  Compiled by tests/test_logic_host.py.
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "philox.cuh"
 #include "rsos_device.cuh"
 #include "rsos_logic.cuh"
@@ -169,4 +172,90 @@ extern "C" long long probe_window_check(int L, int T, int NW, int B, int NWT, lo
         case 16: return window_check<8>(L, NW, B, NWT, n_checked);
         default: return -1;
     }
+}
+
+// (+1) tilings (section III.C): geometry helpers and the window address
+// arithmetic of the general phase kernel.
+#include "rsos_general.cuh"
+
+extern "C" {
+
+void probe_gen_half(int L, int T, int c, int half, int* out2)
+{
+    rsos::gen_half(rsos::gen_axis(L, T), c, half, out2[0], out2[1]);
+}
+
+int probe_gen_valid(int L, int T) { return rsos::gen_axis_valid(L, T) ? 1 : 0; }
+
+int probe_gen_period(int L, int T) { return rsos::gen_period(L, T); }
+
+void probe_gen_locate(int L, int Tx, int Ty, int ox, int oy, int* out4)
+{
+    const rsos::GenOrigin o = rsos::gen_locate_origin_site(L, rsos::gen_tiling(L, Tx, Ty), ox, oy);
+    out4[0] = o.tx; out4[1] = o.ty; out4[2] = o.q; out4[3] = o.k;
+}
+
+// gen_div(k, gen_inv(w)) == k / w for every w in 1..16 and k < 4096.
+long long probe_gen_div_check(void)
+{
+    long long bad = 0;
+    for (uint32_t w = 1; w <= 16; ++w)
+        for (uint32_t k = 0; k < 4096; ++k) bad += rsos::gen_div(k, rsos::gen_inv(w)) != k / w;
+    return bad;
+}
+
+// For every origin of one period, set q, tile and lane-word group: every
+// non-corner window slot's word offset (gen_window_word + plane b + word w)
+// is in range and is the word of site ((ox + u0 + ii - 1) mod L,
+// (oy + v0 + jj - 1) mod L); the interior slots of the four sets cover every
+// site exactly once; the slot gen_locate_origin_site names is site (0,0).
+// Returns the number of failures; *n_checked = checks made.
+long long probe_gen_window_check(int L, int Tx, int Ty, int NW, int B, int NWT, long long* n_checked)
+{
+    const rsos::GenTiling G = rsos::gen_tiling(L, Tx, Ty);
+    const size_t rec_words = (size_t)B * NW;
+    const long long total = (long long)B * L * L * NW;
+    const int px = rsos::gen_period(L, Tx), py = rsos::gen_period(L, Ty);
+    std::vector<int> cover((size_t)L * L);
+    long long bad = 0, n = 0;
+    for (int oy = 0; oy < py; ++oy)
+        for (int ox = 0; ox < px; ++ox) {
+            std::fill(cover.begin(), cover.end(), 0);
+            const rsos::GenOrigin o = rsos::gen_locate_origin_site(L, G, ox, oy);
+            for (int q = 0; q < 4; ++q)
+                for (int ty = 0; ty < G.y.n; ++ty)
+                    for (int tx = 0; tx < G.x.n; ++tx) {
+                        int u0, sw, v0, sh;
+                        rsos::gen_half(G.x, tx, q & 1, u0, sw);
+                        rsos::gen_half(G.y, ty, q >> 1, v0, sh);
+                        for (int jj = 0; jj < sh + 2; ++jj)
+                            for (int ii = 0; ii < sw + 2; ++ii) {
+                                const bool edge_row = jj == 0 || jj == sh + 1, edge_col = ii == 0 || ii == sw + 1;
+                                if (edge_row && edge_col) continue;
+                                const int x = ((ox + u0 + ii - 1) % L + L) % L;
+                                const int y = ((oy + v0 + jj - 1) % L + L) % L;
+                                if (!edge_row && !edge_col) {
+                                    cover[(size_t)y * L + x] += 1;
+                                    const int k = (jj - 1) * sw + (ii - 1);
+                                    const bool is00 = x == 0 && y == 0;
+                                    const bool named = q == o.q && tx == o.tx && ty == o.ty && k == o.k;
+                                    bad += is00 != named;
+                                }
+                                for (int w0 = 0; w0 + NWT <= NW; w0 += NWT) {
+                                    const size_t base = rsos::gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0);
+                                    for (int b = 0; b < B; ++b)
+                                        for (int w = 0; w < NWT; ++w) {
+                                            const long long want = (((long long)y * L + x) * B + b) * NW + w0 + w;
+                                            const long long got = (long long)base + (long long)b * NW + w;
+                                            bad += (got != want || got < 0 || got >= total) ? 1 : 0;
+                                            ++n;
+                                        }
+                                }
+                            }
+                    }
+            for (int v : cover) bad += v != 1;
+        }
+    *n_checked = n;
+    return bad;
+}
 }

@@ -1,0 +1,108 @@
+"""(+1) tilings of the decomposition check (section III.C: 6(+1) x 10(+1)
+domains) on the GPU against the oracle, bit for bit: sums, W^2 and heights
+of every lane.  Plus: with T even and dividing L the general engine is the
+regular tiling (bit-identical to the regular engines, up to L = 4096); the
+paper's largest lattice, L = 9605, against the oracle on sampled lanes; and a
+checkpoint round trip."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1605_02620_gb300 as R
+from rsos_testlib import assert_parity, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L,N,S,T,order,t_end", [
+    (64, 1, 64, (6, 10), 0, 30),    # the paper's 6(+1) x 10(+1) at its smallest L
+    (64, 3, 32, (6, 10), 0, 25),    # 3 planes, one 32-bit lane word
+    (37, 2, 96, (4, 5), 0, 30),     # three lane words (32-bit), ragged tiles on both axes
+    (50, 1, 128, (8, 8), 1, 30),    # 8(+1), fixed phase order, 64-bit words in pairs
+    (27, 7, 64, (3, 9), 0, 20),     # odd regular tiles (T divides L): halves 1 + 2, 4 + 5
+    (13, 2, 2048, (2, 2), 0, 12),   # 64 lane words; halves of 1 and 2 sites
+    (9, 1, 64, (2, 3), 0, 40),      # one axis irregular, the other regular and odd
+    (61, 4, 64, (30, 30), 0, 8),    # the widest tiles: halves of 15 and 16 sites
+])
+def test_general_tiling_matches_oracle(L, N, S, T, order, t_end):
+    times = sorted({0, 1, 3, t_end // 2, t_end})
+    assert_parity(L, N, S, T, seed=41 + L + N, order=order, times=times, t_end=t_end, tiling=1)
+
+
+@pytest.mark.parametrize("L,N,S,T", [(256, 1, 64, 8), (128, 2, 32, 4), (64, 5, 64, 16)])
+def test_divisible_tiles_equal_the_regular_engines(L, N, S, T):
+    kw = dict(L=L, N=N, S=S, T=T, seed=7, times=[0, 3, 11], t_end=11, height_lanes=[0, S - 1])
+    g = gpu_run(tiling=1, **kw)
+    for engine in (1, 2) if L // T >= 8 else (1,):
+        r = gpu_run(engine=engine, **kw)
+        assert (g[1] == r[1]).all() and (g[2] == r[2]).all(), engine
+        for j in (0, S - 1):
+            assert np.array_equal(g[4][j], r[4][j]), (engine, j)
+
+
+def test_divisible_tiles_equal_the_persistent_engine_full_size():
+    kw = dict(L=4096, N=1, S=64, T=8, seed=9, times=[0, 1, 7, 20], t_end=20, height_lanes=[0, 40])
+    g = gpu_run(tiling=1, **kw)
+    r = gpu_run(engine=2, **kw)
+    assert (g[1] == r[1]).all() and (g[2] == r[2]).all()
+    for j in (0, 40):
+        assert np.array_equal(g[4][j], r[4][j])
+
+
+def test_L9605_against_oracle_on_sampled_lanes():
+    """L = 9605 (the paper's largest lattice; not a multiple of 6 or 10),
+    6(+1) x 10(+1), 64 surfaces: two lanes' sums and every height after 2
+    sweeps equal the oracle's."""
+    L, t_end, lanes = 9605, 2, [0, 45]
+    gts, g1, g2, gw, gh = gpu_run(L, 1, 64, (6, 10), seed=5, times=[0, 1, 2], t_end=t_end, height_lanes=lanes,
+                                  tiling=1)
+    p = O.Params(L=L, N=1, Tx=6, Ty=10, seed=5, tiling=1)
+    ts, o1, o2, oh = O.run_series(p, lanes, [0, 1, 2], threads=2)
+    assert list(gts) == ts
+    for m in range(len(ts)):
+        for c, j in enumerate(lanes):
+            assert int(g1[m, j]) == int(o1[m][c]) and int(g2[m, j]) == int(o2[m][c]), (ts[m], j)
+    for c, j in enumerate(lanes):
+        assert np.array_equal(gh[j], oh[c]), j
+
+
+def test_L9605_longer_run_properties():
+    """After 40 sweeps at L = 9605: every neighbour difference of the read-back
+    heights is within N (Eq. 6, periodic), and their exact sums are the
+    measured ones."""
+    L, N, S = 9605, 2, 32
+    gts, g1, g2, gw, gh = gpu_run(L, N, S, (6, 10), seed=8, times=[40], t_end=40, height_lanes=[0, 31],
+                                  tiling=1)
+    for j in (0, 31):
+        h = gh[j].astype(np.int64)
+        assert np.abs(h - np.roll(h, 1, axis=0)).max() <= N
+        assert np.abs(h - np.roll(h, 1, axis=1)).max() <= N
+        assert int(h.sum()) == int(g1[0, j])
+        assert int((h * h).sum()) == int(g2[0, j])
+        assert h.sum() > 0.3 * 40 * L * L  # it grew
+
+
+def test_checkpoint_round_trip():
+    times = [0, 2, 5, 9]
+    p = R.rsos_params(L=64, N=1, surfaces=64, tile=(6, 10), seed=3, series_capacity=8, tiling=1)
+    a = R.rsos_init(p)
+    R.rsos_schedule(a, times)
+    R.rsos_sweep(a, 9)
+    ref = R.rsos_read_series(a, 64, 8)
+    ref_h = R.rsos_heights(a, 17, 64)
+    R.rsos_free(a)
+    b = R.rsos_init(p)
+    R.rsos_schedule(b, times)
+    R.rsos_sweep(b, 4)
+    snap = R.rsos_snapshot(b)
+    R.rsos_free(b)
+    c = R.rsos_restore(snap)
+    try:
+        R.rsos_sweep(c, 5)
+        got = R.rsos_read_series(c, 64, 8)
+        got_h = R.rsos_heights(c, 17, 64)
+    finally:
+        R.rsos_free(c)
+    assert list(got[0]) == list(ref[0]) == times
+    assert (got[1] == ref[1]).all() and (got[2] == ref[2]).all()
+    assert np.array_equal(got_h, ref_h)
