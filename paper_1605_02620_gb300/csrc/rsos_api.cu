@@ -266,10 +266,11 @@ int run_sweep_general(rsos_handle* h, cudaStream_t s)
                             rsos::gen_period(L, h->p.tile_y), h->p.phase_order);
     const rsos::GenOrigin o = rsos::gen_locate_origin_site(L, h->G, c.ox, c.oy);
     for (int p = 0; p < 4; ++p) {
+        int n = 0;
         const cudaError_t e =
-            rsos::launch_phase_general(h->J, h->G, h->NWT, t, p, c.perm[p], c.ox, c.oy, o, h->smem_budget, s);
+            rsos::launch_phase_general(h->J, h->G, h->NWT, t, p, c.perm[p], c.ox, c.oy, o, h->smem_budget, s, &n);
+        h->launches += n;
         if (e != cudaSuccess) return fail_cuda(h, e);
-        h->launches += 1;
     }
     h->t += 1;
     return RSOS_OK;

@@ -105,58 +105,97 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
 }
 
 template <int N, typename WT>
-__global__ void __launch_bounds__(256) general_phase_kernel(JobDev J, GenTiling G, uint32_t t, int p, int q, int ox,
-                                                            int oy, GenOrigin o)
+__global__ void __launch_bounds__(256) general_phase_kernel(JobDev J, GenTiling G, GenLaunch P, uint32_t t, int p,
+                                                            int q, int ox, int oy, GenOrigin o)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WT* sm = reinterpret_cast<WT*>(smem_raw);
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const long long gid = (long long)blockIdx.x * nthr + tid;
-    const long long per_row = (long long)G.x.n * J.NWP;
-    if (gid >= per_row * G.y.n) return;
-    const int ty = (int)(gid / per_row);
-    const int rem = (int)(gid - (long long)ty * per_row);
-    const int tx = rem / J.NWP, wp = rem - tx * J.NWP;
+    const int tid = threadIdx.x;
+    int tx, ty, wp, nthr;
+    if (!gen_item_of_thread(P, J.NWP, (int)blockIdx.x, tid, (int)blockDim.x, tx, ty, wp, nthr)) return;
     if (q == o.q && tx == o.tx && ty == o.ty)
         general_activate<N, WT, true>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, o.k);
     else
         general_activate<N, WT, false>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, -1);
 }
 
+// Threads per block that keep the most threads resident per SM for windows
+// of per_thread bytes (shared memory is the limit; ties go to larger blocks).
+template <int N, typename WT>
+int general_block_threads(size_t per_thread, size_t smem_cap)
+{
+    int best = 32, best_resident = -1;
+    for (int n = 32; n <= 256; n += 32) {
+        const size_t smem = per_thread * (size_t)n;
+        if (smem > smem_cap) break;
+        if (cudaFuncSetAttribute(general_phase_kernel<N, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            break;
+        }
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, general_phase_kernel<N, WT>, n, smem) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            break;
+        }
+        if (blocks * n >= best_resident) {
+            best_resident = blocks * n;
+            best = n;
+        }
+    }
+    return best;
+}
+
 template <int N, typename WT>
 cudaError_t launch_general_t(const JobDev& J, const GenTiling& G, uint32_t t, int p, int q, int ox, int oy,
-                             const GenOrigin& o, size_t smem_budget, cudaStream_t s)
+                             const GenOrigin& o, size_t smem_budget, cudaStream_t s, int* n_launches)
 {
     constexpr int B = bits_for_step(N);
-    const size_t per_thread = (size_t)(G.max_w + 2) * (G.max_h + 2) * B * sizeof(WT);
-    const long long total = (long long)G.x.n * G.y.n * J.NWP;
-    long long n = (long long)(smem_budget / per_thread) / 32 * 32;
-    if (n > 256) n = 256;
-    if (n < 32) n = 32;
-    const size_t smem = per_thread * (size_t)n;
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(general_phase_kernel<N, WT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
+    *n_launches = 0;
+    const size_t wbytes = (size_t)B * sizeof(WT);  // one window slot
+    const size_t pt_narrow = gen_narrow_window_slots(G) * wbytes;
+    const size_t pt_wide = (size_t)(G.max_w + 2) * (G.max_h + 2) * wbytes;
+    if (pt_wide * 8 > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const size_t cap = smem_budget < pt_narrow * 32 ? pt_narrow * 32 : smem_budget;
+    // block size per (window bytes, budget), remembered for a few windows
+    struct Plan {
+        size_t per_thread, cap;
+        int n;
+    };
+    static Plan plans[8] = {};
+    static int n_plans = 0;
+    int n = 0;
+    for (int k = 0; k < n_plans; ++k)
+        if (plans[k].per_thread == pt_narrow && plans[k].cap == cap) n = plans[k].n;
+    if (n == 0) {
+        n = general_block_threads<N, WT>(pt_narrow, cap > 227 * 1024 ? 227 * 1024 : cap);
+        if (n_plans < 8) plans[n_plans++] = Plan{pt_narrow, cap, n};
     }
-    const long long blocks = (total + n - 1) / n;
-    general_phase_kernel<N, WT><<<(unsigned)blocks, (unsigned)n, smem, s>>>(J, G, t, p, q, ox, oy, o);
+    GenLaunch P;
+    size_t smem = 0;
+    long long blocks = 0;
+    gen_plan_launch(G, J.NWP, wbytes, n, P, smem, blocks);
+    if (blocks == 0) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(general_phase_kernel<N, WT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    general_phase_kernel<N, WT><<<(unsigned)blocks, (unsigned)n, smem, s>>>(J, G, P, t, p, q, ox, oy, o);
+    *n_launches = 1;
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_per_thread, uint32_t t, int p, int q,
-                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s)
+                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s,
+                                 int* n_launches)
 {
-#define RSOS_CASE(NN)                                                                             \
-    case NN:                                                                                      \
-        return words_per_thread == 2                                                              \
-                   ? launch_general_t<NN, uint64_t>(J, G, t, p, q, ox, oy, o, smem_budget, s)     \
-                   : launch_general_t<NN, uint32_t>(J, G, t, p, q, ox, oy, o, smem_budget, s);
+#define RSOS_CASE(NN)                                                                                      \
+    case NN:                                                                                               \
+        return words_per_thread == 2                                                                       \
+                   ? launch_general_t<NN, uint64_t>(J, G, t, p, q, ox, oy, o, smem_budget, s, n_launches) \
+                   : launch_general_t<NN, uint32_t>(J, G, t, p, q, ox, oy, o, smem_budget, s, n_launches);
     switch (J.N) {
         RSOS_CASE(1)
         RSOS_CASE(2)

@@ -135,4 +135,90 @@ RSOS_HD GenOrigin gen_locate_origin_site(int L, const GenTiling& G, int ox, int 
     return o;
 }
 
+// Rectangle of tiles [x0, x0 + nx) x [y0, y0 + ny).
+struct GenRect {
+    int32_t x0, nx, y0, ny;
+};
+
+// One phase launch.  Along each axis the tiles of index >= r are all T wide,
+// so windows for halves of ceil(T/2) serve them ("narrow" blocks, blockDim
+// threads each); the rows and columns of (T + 1) tiles ("wide" rectangles)
+// run in the last blocks of the same launch with fewer active threads
+// (n_wide, a multiple of 8 so slots stay bank-conflict free), so their larger
+// windows fit the same shared memory.  One thread per (tile, lane-word group).
+struct GenLaunch {
+    GenRect narrow, wide[2];
+    int32_t nb_narrow;  // blocks of the narrow rectangle
+    int32_t n_wide;     // active threads (and slot stride) of a wide block
+};
+
+// Window slots of a thread of a narrow block.
+RSOS_HD size_t gen_narrow_window_slots(const GenTiling& G)
+{
+    return (size_t)(((G.x.T + 1) >> 1) + 2) * (size_t)(((G.y.T + 1) >> 1) + 2);
+}
+
+// Launch plan for n threads per block and slots of wbytes bytes: the
+// rectangles, the block counts, and the dynamic shared memory per block.
+RSOS_HD void gen_plan_launch(const GenTiling& G, int NWP, size_t wbytes, int n, GenLaunch& P, size_t& smem,
+                             long long& blocks)
+{
+    const int nw = (G.x.T + 1) >> 1, nh = (G.y.T + 1) >> 1;
+    if (nw == G.max_w && nh == G.max_h) {
+        P.narrow = GenRect{0, G.x.n, 0, G.y.n};
+        P.wide[0] = P.wide[1] = GenRect{0, 0, 0, 0};
+    } else {
+        P.narrow = GenRect{G.x.r, G.x.n - G.x.r, G.y.r, G.y.n - G.y.r};
+        P.wide[0] = GenRect{0, G.x.r, 0, G.y.n};
+        P.wide[1] = GenRect{G.x.r, G.x.n - G.x.r, 0, G.y.r};
+    }
+    const size_t pt_narrow = gen_narrow_window_slots(G) * wbytes;
+    const size_t pt_wide = (size_t)(G.max_w + 2) * (size_t)(G.max_h + 2) * wbytes;
+    smem = pt_narrow * (size_t)n;
+    const long long narrow_items = (long long)P.narrow.nx * P.narrow.ny * NWP;
+    const long long wide_items =
+        ((long long)P.wide[0].nx * P.wide[0].ny + (long long)P.wide[1].nx * P.wide[1].ny) * NWP;
+    P.nb_narrow = (int32_t)((narrow_items + n - 1) / n);
+    int nwide = (int)(smem / pt_wide) / 8 * 8;
+    if (nwide < 8) nwide = 8;
+    if (nwide > n) nwide = n;
+    P.n_wide = nwide;
+    if ((size_t)nwide * pt_wide > smem) smem = (size_t)nwide * pt_wide;
+    blocks = P.nb_narrow + (wide_items + nwide - 1) / nwide;
+}
+
+// Tile (tx, ty), lane-word group wp and slot stride nthr of thread tid of
+// block b (blockDim threads); false if the thread has no work.
+RSOS_HD bool gen_item_of_thread(const GenLaunch& P, int NWP, int b, int tid, int blockDim, int& tx, int& ty, int& wp,
+                                int& nthr)
+{
+    long long g;
+    GenRect R;
+    if (b < P.nb_narrow) {
+        nthr = blockDim;
+        g = (long long)b * nthr + tid;
+        R = P.narrow;
+        if (g >= (long long)R.nx * R.ny * NWP) return false;
+    } else {
+        nthr = P.n_wide;
+        if (tid >= nthr) return false;
+        g = (long long)(b - P.nb_narrow) * nthr + tid;
+        R = P.wide[0];
+        const long long n0 = (long long)R.nx * R.ny * NWP;
+        if (g >= n0) {
+            g -= n0;
+            R = P.wide[1];
+            if (g >= (long long)R.nx * R.ny * NWP) return false;
+        }
+    }
+    const long long per_row = (long long)R.nx * NWP;
+    const int ry = (int)(g / per_row);
+    const int rem = (int)(g - (long long)ry * per_row);
+    const int rx = rem / NWP;
+    wp = rem - rx * NWP;
+    tx = R.x0 + rx;
+    ty = R.y0 + ry;
+    return true;
+}
+
 }  // namespace rsos

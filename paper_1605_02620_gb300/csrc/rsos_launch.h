@@ -19,8 +19,10 @@ cudaError_t launch_phase_plain(const JobDev& J, int SX, uint32_t t, int p, int q
 
 // One phase on a (+1) tiling (section III.C): sub-tile set q = perm[p] of
 // every tile of G; o locates site (0,0) in this sweep's tiling.
+// *n_launches = kernels queued (1).
 cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_per_thread, uint32_t t, int p, int q,
-                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s);
+                                 int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s,
+                                 int* n_launches);
 
 #define RSOS_DECLARE_SX(SX)                                                                          \
     cudaError_t launch_phase_s##SX(const JobDev& J, int words_per_thread, uint32_t t, int p, int q,  \

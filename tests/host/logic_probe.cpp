@@ -259,3 +259,45 @@ long long probe_gen_window_check(int L, int Tx, int Ty, int NW, int B, int NWT, 
     return bad;
 }
 }
+
+extern "C" {
+
+// Launch plan of the general phase kernel for n threads per block: every
+// (tile, lane-word group) is taken by exactly one thread; every thread's
+// window, for either half on both axes, lies inside the block's dynamic
+// shared memory at its slot stride; slot strides are multiples of 8 (bank
+// conflict free).  Returns failures; out3 = (blocks, n_wide, smem bytes).
+long long probe_gen_plan_check(int L, int Tx, int Ty, int NWP, int wbytes, int n, long long* out3)
+{
+    const rsos::GenTiling G = rsos::gen_tiling(L, Tx, Ty);
+    rsos::GenLaunch P;
+    size_t smem = 0;
+    long long blocks = 0;
+    rsos::gen_plan_launch(G, NWP, (size_t)wbytes, n, P, smem, blocks);
+    out3[0] = blocks;
+    out3[1] = P.n_wide;
+    out3[2] = (long long)smem;
+    std::vector<int> seen((size_t)G.x.n * G.y.n * NWP);
+    long long bad = 0;
+    for (long long b = 0; b < blocks; ++b)
+        for (int tid = 0; tid < n; ++tid) {
+            int tx, ty, wp, nthr;
+            if (!rsos::gen_item_of_thread(P, NWP, (int)b, tid, n, tx, ty, wp, nthr)) continue;
+            if (tx < 0 || tx >= G.x.n || ty < 0 || ty >= G.y.n || wp < 0 || wp >= NWP || tid >= nthr || nthr % 8) {
+                ++bad;
+                continue;
+            }
+            seen[((size_t)ty * G.x.n + tx) * NWP + wp] += 1;
+            for (int q = 0; q < 4; ++q) {
+                int u0, sw, v0, sh;
+                rsos::gen_half(G.x, tx, q & 1, u0, sw);
+                rsos::gen_half(G.y, ty, q >> 1, v0, sh);
+                const size_t last_slot = (size_t)(sw + 2) * (sh + 2) - 1;
+                const size_t end = ((last_slot * nthr + tid) + 1) * (size_t)wbytes;
+                bad += end > smem;
+            }
+        }
+    for (int v : seen) bad += v != 1;
+    return bad;
+}
+}

@@ -183,3 +183,19 @@ def test_general_window_addresses_exhaustive(probe, L, Tx, Ty, NW, B, NWT):
     n = ctypes.c_longlong()
     bad = probe.probe_gen_window_check(L, Tx, Ty, NW, B, NWT, ctypes.byref(n))
     assert bad == 0 and n.value > 0
+
+
+@pytest.mark.parametrize("L,Tx,Ty,NWP,wbytes,n", [
+    (9605, 6, 10, 1, 16, 96), (9605, 6, 10, 1, 16, 128), (64, 6, 10, 2, 8, 64), (37, 4, 5, 3, 12, 32),
+    (50, 8, 8, 2, 16, 256), (27, 3, 9, 1, 16, 64), (13, 2, 2, 32, 24, 96), (61, 30, 30, 2, 16, 32),
+    (256, 8, 8, 1, 16, 192), (9, 2, 3, 1, 16, 32),
+])
+def test_general_launch_plan_covers_every_tile_once(probe, L, Tx, Ty, NWP, wbytes, n):
+    """The general kernel's blocks (narrow, then wide with fewer threads)
+    take every tile and lane-word group once, and every window fits the
+    block's shared memory at its thread's slot stride."""
+    probe.probe_gen_plan_check.argtypes = [ctypes.c_int] * 6 + [ctypes.POINTER(ctypes.c_longlong)]
+    probe.probe_gen_plan_check.restype = ctypes.c_longlong
+    out = (ctypes.c_longlong * 3)()
+    assert probe.probe_gen_plan_check(L, Tx, Ty, NWP, wbytes, n, out) == 0
+    assert out[0] > 0 and out[1] % 8 == 0 and out[2] <= 227 * 1024
