@@ -279,7 +279,10 @@ int rsos_advance(rsos_handle* const* jobs, const int64_t* t_target, int32_t n, v
 /* Create a batch of n_jobs jobs (params[i], t_max[i] sweeps each) whose device
  * memory must fit hbm_budget bytes (0 = no limit).  Each job starts flat at
  * t = 0; its width is measured at t_max (and at the times of its schedule, if
- * set with rsos_batch_schedule).  RSOS_ENOMEM if the budget is exceeded. */
+ * set with rsos_batch_schedule).  Regular multisurface jobs share the
+ * multi-job persistent launches; single-surface jobs and (+1) tilings run
+ * through their own handles inside the batch.  RSOS_ENOMEM if the budget is
+ * exceeded. */
 int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n_jobs,
                       size_t hbm_budget, rsos_batch** out);
 

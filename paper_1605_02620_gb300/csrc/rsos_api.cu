@@ -1085,7 +1085,9 @@ int rsos_batch_create(const rsos_params* params, const int64_t* t_max, int32_t n
     size_t total = 0;
     for (int32_t i = 0; i < n_jobs; ++i) {
         if (t_max[i] < 0 || t_max[i] > kMaxSweeps) return RSOS_EINVAL;
-        if (ps[i].surfaces > 1 && ps[i].engine == 0) {
+        // regular multisurface jobs join the multi-job persistent launches;
+        // plain jobs and (+1) tilings run through their own handles
+        if (ps[i].surfaces > 1 && ps[i].engine == 0 && ps[i].tiling == 0) {
             const int NW = (ps[i].surfaces + 31) / 32;
             if (NW / words_per_thread(&ps[i], NW) <= 32) ps[i].engine = 2;
         }

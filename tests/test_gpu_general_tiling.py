@@ -2,8 +2,9 @@
 domains) on the GPU against the oracle, bit for bit: sums, W^2 and heights
 of every lane.  Plus: with T even and dividing L the general engine is the
 regular tiling (bit-identical to the regular engines, up to L = 4096); the
-paper's largest lattice, L = 9605, against the oracle on sampled lanes; and a
-checkpoint round trip."""
+paper's largest lattice, L = 9605, against the oracle on sampled lanes; a
+checkpoint round trip; exact power sums; batches, rsos_advance and the
+no-allocation width on (+1)-tiling jobs."""
 import numpy as np
 import pytest
 
@@ -106,3 +107,83 @@ def test_checkpoint_round_trip():
     assert list(got[0]) == list(ref[0]) == times
     assert (got[1] == ref[1]).all() and (got[2] == ref[2]).all()
     assert np.array_equal(got_h, ref_h)
+
+
+def test_power_sums_match_oracle():
+    """Sum h^3, sum h^4 (section III.C moments) on a (+1) tiling, exactly."""
+    L, N, S, t_end, times = 64, 2, 64, 15, [0, 4, 15]
+    p = R.rsos_params(L=L, N=N, surfaces=S, tile=(6, 10), seed=13, series_capacity=8, tiling=1)
+    h = R.rsos_init(p)
+    try:
+        R.rsos_set_moments(h, True)
+        R.rsos_schedule(h, times)
+        R.rsos_sweep(h, t_end)
+        ts, sums, has = R.rsos_read_moments(h, S, 8)
+    finally:
+        R.rsos_free(h)
+    ots, _, _, _, ops = O.run_series(O.Params(L=L, N=N, Tx=6, Ty=10, seed=13, tiling=1), list(range(S)), times,
+                                     powers=True)
+    assert list(ts) == ots and has.all()
+    for m in range(len(ots)):
+        for j in range(S):
+            assert list(sums[m, j]) == ops[m][j], (ots[m], j)
+
+
+def test_batch_and_advance_run_general_jobs():
+    """(+1)-tiling jobs in a batch (beside regular jobs) and through
+    rsos_advance give what they give alone."""
+    import torch
+    jobs = [(64, 1, 64, (6, 10), 1, 20), (128, 1, 64, 8, 0, 15), (37, 2, 96, (4, 5), 1, 12)]
+    params = [R.rsos_params(L=L, N=N, surfaces=S, tile=T, seed=k, series_capacity=4, tiling=tl)
+              for k, (L, N, S, T, tl, t) in enumerate(jobs)]
+    b = R.rsos_batch_create(params, [t for (*_, t) in jobs])
+    try:
+        R.rsos_batch_run(b, torch.cuda.Stream())
+        done = set()
+        for _ in range(200000):
+            rc, ids = R.rsos_batch_poll(b)
+            done |= set(ids)
+            if len(done) == len(jobs):
+                break
+        assert len(done) == len(jobs)
+        got = [R.rsos_read_series(R.rsos_batch_job(b, k), jobs[k][2], 4) for k in range(len(jobs))]
+    finally:
+        R.rsos_batch_free(b)
+    handles = [R.rsos_init(p) for p in params]
+    try:
+        for h, (*_, t) in zip(handles, jobs):
+            R.rsos_schedule(h, [t])
+        R.rsos_advance(handles, [t for (*_, t) in jobs])
+        adv = [R.rsos_read_series(h, jobs[k][2], 4) for k, h in enumerate(handles)]
+    finally:
+        for h in handles:
+            R.rsos_free(h)
+    for k, (L, N, S, T, tl, t) in enumerate(jobs):
+        _, a1, a2, _, _ = gpu_run(L, N, S, T, seed=k, times=[t], t_end=t, tiling=tl)
+        for res in (got[k], adv[k]):
+            assert list(res[0]) == [t]
+            assert (res[1] == a1).all() and (res[2] == a2).all(), k
+
+
+def test_noalloc_width_on_general_layout():
+    """rsos_width_noalloc reads the row-major records of a (+1) tiling."""
+    import torch
+    L, S = 64, 64
+    p = R.rsos_params(L=L, N=1, surfaces=S, tile=(6, 10), seed=21, series_capacity=4, tiling=1)
+    nbytes = R.rsos_required_bytes(p)
+    buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (buf.data_ptr() + 255) // 256 * 256
+    h00_off = (2 * L * L * 2 * 4 + 255) // 256 * 256
+    out = torch.zeros(S * 4, dtype=torch.int64, device="cuda")
+    h = R.rsos_init(p, dev_buf=base, dev_bytes=nbytes)
+    try:
+        R.rsos_sweep(h, 9)
+        s1, s2, _, _ = R.rsos_width(h, S)
+        R.rsos_width_noalloc(p, base, base + h00_off, out.data_ptr())
+        torch.cuda.synchronize()
+    finally:
+        R.rsos_free(h)
+    v = out.cpu().numpy().reshape(S, 4)
+    to128 = lambda lo, hi: [(int(b) << 64) + (int(a) & 0xFFFFFFFFFFFFFFFF) for a, b in zip(lo, hi)]
+    assert to128(v[:, 0], v[:, 1]) == [int(x) for x in s1]
+    assert to128(v[:, 2], v[:, 3]) == [int(x) for x in s2]
