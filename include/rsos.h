@@ -88,7 +88,7 @@ typedef struct rsos_batch rsos_batch;
  *                else L).  With T even and dividing L it is the regular
  *                tiling, bit for bit.  Multisurface jobs (surfaces >= 2) on
  *                the one-launch-per-phase engine (engine 0 or 1) only; the
- *                lattice is stored with site records in row-major order.   */
+ *                lattice rows hold T ceil(L / T) site records (T = tile_x). */
 typedef struct {
     int32_t L;
     int32_t N;

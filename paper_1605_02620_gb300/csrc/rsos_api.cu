@@ -69,6 +69,7 @@ thread_local int g_init_cuda_err = 0;
 struct Layout {
     size_t planes, h00, row0, partial, rec, persist, total;
     int ncb, S_pad, B, NW, T, cap;
+    int nTc;    // class columns per row of the layout
     int CW, K;  // persistent engine: tiles per block, chunks per tile row
     bool plain, persist_on;
 };
@@ -158,12 +159,20 @@ int validate(const rsos_params* p)
     return RSOS_OK;
 }
 
+// Bytes of the coded lattice: int32 heights (plain), or L rows of T nTc
+// site records (a (+1) tiling pads each row to whole class columns).
+size_t lattice_bytes(const Layout& l, size_t L)
+{
+    return l.plain ? L * L * 4 : (size_t)l.B * L * (size_t)l.T * (size_t)l.nTc * l.NW * 4;
+}
+
 Layout layout_of(const rsos_params* p)
 {
     Layout l;
-    // Layout tile edge: the class interleaving of the regular tiling, or
-    // row-major site records (edge 1) for the (+1) tilings.
-    l.T = p->tiling == 1 ? 1 : (p->tile_x == 0 ? 8 : p->tile_x);
+    // Layout tile edge: column classes of the (x) tile edge; a (+1) tiling
+    // keeps ceil(L / T) class columns per row (the last ones partly unused).
+    l.T = p->tile_x == 0 ? 8 : p->tile_x;
+    l.nTc = p->tiling == 1 ? rsos::gen_classes(p->L, l.T) : p->L / l.T;
     l.plain = p->surfaces == 1;
     l.B = rsos::bits_for_step(p->N);
     l.NW = (p->surfaces + 31) / 32;
@@ -173,10 +182,10 @@ Layout layout_of(const rsos_params* p)
     JobDev J{};
     J.L = p->L;
     J.T = l.T;
-    J.nT = p->L / l.T;
+    J.nT = l.nTc;
     J.NW = l.NW;
     l.ncb = rsos::measure_blocks(J, l.plain);
-    l.planes = align256(l.plain ? L * L * 4 : (size_t)l.B * L * L * l.NW * 4);
+    l.planes = align256(lattice_bytes(l, L));
     l.h00 = align256((size_t)l.S_pad * 8);
     l.row0 = l.plain ? 0 : align256((size_t)l.S_pad * L * 4);
     l.partial = align256((size_t)l.ncb * l.S_pad * 6 * 8);  // moments need 6 words per entry
@@ -537,7 +546,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     }
     J.L = params->L;
     J.T = l.T;
-    J.nT = params->L / l.T;
+    J.nT = l.nTc;
     J.NW = l.NW;
     J.NWP = l.NW / h->NWT;
     J.N = params->N;
@@ -1409,7 +1418,8 @@ size_t pad8(size_t v) { return (v + 7) & ~(size_t)7; }
 size_t lattice_bytes_of(const rsos_handle* h)
 {
     const size_t L = (size_t)h->p.L;
-    return h->plain ? L * L * 4 : (size_t)h->B * L * L * h->NW * 4;
+    // multisurface: L rows of T nT records (a (+1) tiling pads each row)
+    return h->plain ? L * L * 4 : (size_t)h->B * L * (size_t)h->J.T * (size_t)h->J.nT * h->NW * 4;
 }
 
 size_t snapshot_size(const rsos_handle* h)
@@ -1488,7 +1498,7 @@ extern "C" int rsos_restore(const void* host_buf, size_t bytes, void* dev_buf, s
         return RSOS_EINVAL;
     const Layout l = layout_of(&hd.params);
     const size_t L = (size_t)hd.params.L;
-    const size_t lattice = l.plain ? L * L * 4 : (size_t)l.B * L * L * l.NW * 4;
+    const size_t lattice = lattice_bytes(l, L);
     const size_t n = (size_t)hd.n_series;
     if (hd.lattice_bytes != lattice || hd.h00_bytes != (size_t)l.S_pad * 8 || (int)n > l.cap ||
         hd.series_bytes != n * l.S_pad * kRecWords * 8)

@@ -2,7 +2,9 @@
 // decomposition check (section III.C): one launch activates sub-tile set
 // q = perm[p] of every tile, one thread per (tile, lane-word group), as the
 // regular phase kernel does, with the tile and sub-tile extents taken at run
-// time (T or T + 1 wide tiles, halves of floor(w/2) and the rest).  Each
+// time (T or T + 1 wide tiles, halves of floor(w/2) and the rest), over the
+// class-interleaved site records of the regular tiling (column classes of
+// the x base edge).  Each
 // selection is Eq. 6 on bit-sliced words; the stream is the regular one with
 // a = the sub-tile's own area: 2a selections per activation, site index
 // k = floor(u a / 2^16) of a 16-bit u, kx = k mod w, ky = k div w.
@@ -31,14 +33,18 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
     const bool whole_record = NWT == J.NW;
     const size_t rs = (size_t)nthr * B;  // one slot
 
-    // Stage the sub-tile and its one-site halo (corners unused).
-    for (int jj = 0; jj < sh + 2; ++jj) {
-        const bool edge_row = jj == 0 || jj == sh + 1;
-        for (int ii = edge_row ? 1 : 0; ii < (edge_row ? sw + 1 : sw + 2); ++ii) {
+    // Stage the sub-tile and its one-site halo (corners unused), column by
+    // column: window column ii is lattice column ox + u0 + ii - 1.
+    GenCol col = gen_col(L, J.T, ox + u0 - 1);
+    for (int ii = 0; ii < sw + 2; ++ii) {
+        const size_t cw = gen_col_words(col, J.nT, rec_words) + (size_t)w0;
+        const bool edge_col = ii == 0 || ii == sw + 1;
+        for (int jj = edge_col ? 1 : 0; jj < (edge_col ? sh + 1 : sh + 2); ++jj) {
             WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
-            stage_record_async<WT, B>(slot, J.planes + gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0),
-                                      J.NW, whole_record);
+            const size_t rw = gen_row_words(L, J.T, J.nT, rec_words, oy + v0 + jj - 1);
+            stage_record_async<WT, B>(slot, J.planes + rw + cw, J.NW, whole_record);
         }
+        gen_col_next(col, L, J.T);
     }
     stage_wait_all();
 
@@ -83,10 +89,13 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
     }
 
     // Write the interior back.
-    for (int jj = 1; jj <= sh; ++jj) {
-        for (int ii = 1; ii <= sw; ++ii) {
+    col = gen_col(L, J.T, ox + u0);
+    for (int ii = 1; ii <= sw; ++ii) {
+        const size_t cw = gen_col_words(col, J.nT, rec_words) + (size_t)w0;
+        gen_col_next(col, L, J.T);
+        for (int jj = 1; jj <= sh; ++jj) {
             const WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
-            uint32_t* dst = J.planes + gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0);
+            uint32_t* dst = J.planes + gen_row_words(L, J.T, J.nT, rec_words, oy + v0 + jj - 1) + cw;
             WT v[B];
             load_rec<B, WT>(slot, v);
             if (B * sizeof(WT) == 16 && whole_record) {

@@ -10,9 +10,13 @@
 // when T divides L, else after L: the per-sweep origin is uniform over that
 // period.  With T even and dividing L this is the regular tiling.
 //
-// Lattice layout for these tilings: site records in row-major order (record
-// index y L + x), the layout of the regular tiling with a tile edge of 1, so
-// the measurement kernels read it unchanged.
+// Lattice layout for these tilings: the regular tiling's, site records
+// interleaved by column class of the x base edge T, record index
+// (y T + x mod T) nT + x div T, with nT = ceil(L / T) class columns per row
+// (when T does not divide L the last class columns of a row stay unused).
+// Tiles of base width are T apart, so for one window slot the records of
+// consecutive tiles are consecutive and a warp's access is one contiguous
+// run; the measurement kernels read this layout unchanged.
 #pragma once
 #include "rsos_common.cuh"
 
@@ -66,16 +70,49 @@ RSOS_HD int gen_wrap(int v, int L)
     return v < 0 ? v + L : (v >= L ? v - L : v);
 }
 
-// Word offset (plane 0, lane word w0) of window slot (ii, jj) of the
-// sub-tile whose first site is pattern coordinate (u0, v0): the record of
-// site ((ox + u0 + ii - 1) mod L, (oy + v0 + jj - 1) mod L) in row-major
-// order, rec_words words per record.  ii, jj = 0 and w + 1, h + 1 are the
-// halo.
-RSOS_HD size_t gen_window_word(int L, size_t rec_words, int ox, int oy, int u0, int v0, int ii, int jj, int w0)
+// Class columns of a row: ceil(L / T).
+RSOS_HD int gen_classes(int L, int T)
 {
-    const size_t x = (size_t)gen_wrap(ox + u0 + ii - 1, L);
-    const size_t y = (size_t)gen_wrap(oy + v0 + jj - 1, L);
-    return (y * (size_t)L + x) * rec_words + (size_t)w0;
+    return (L + T - 1) / T;
+}
+
+// Column x of the lattice with its class coordinates (x = q T + r).  The
+// window loops walk columns with gen_col_next instead of dividing per slot.
+struct GenCol {
+    int32_t x, q, r;
+};
+
+// Column of (unwrapped) coordinate v in [-L, 2L).
+RSOS_HD GenCol gen_col(int L, int T, int v)
+{
+    const int x = gen_wrap(v, L);
+    const int q = x / T;
+    return GenCol{x, q, x - q * T};
+}
+
+// The next column to the east (periodic).
+RSOS_HD void gen_col_next(GenCol& c, int L, int T)
+{
+    if (++c.x == L) {
+        c = GenCol{0, 0, 0};
+        return;
+    }
+    if (++c.r == T) {
+        c.r = 0;
+        ++c.q;
+    }
+}
+
+// Word offset of column c within a row of records (rec_words words each).
+RSOS_HD size_t gen_col_words(const GenCol& c, int nT, size_t rec_words)
+{
+    return ((size_t)c.r * (size_t)nT + (size_t)c.q) * rec_words;
+}
+
+// Word offset of the row of (unwrapped) coordinate v in [-L, 2L).
+RSOS_HD size_t gen_row_words(int L, int T, int nT, size_t rec_words, int v)
+{
+    return (size_t)gen_wrap(v, L) * (size_t)T * (size_t)nT * rec_words;
 }
 
 // floor(k / w) for k < 4096 and 1 <= w <= 16 by a multiply with

@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(256) column_walk_kernel(JobDev J, const int32_
     const int u = cb % T;
     const int col = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const int m = (cb / T) * 32 + col;
-    const bool valid = m < nT;
     const int x = m * T + u;
+    const bool valid = m < nT && x < L;  // (+1) tilings: last class columns partly unused
     const int RL = (L + kSeg - 1) / kSeg;
     const int y0 = min(L, seg * RL), y1 = min(L, y0 + RL);
     int r[8], s1[8], vprev[8];
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(256) column_moments_kernel(JobDev J, const int
     const int u = cb % T;
     const int col = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const int m = (cb / T) * 32 + col;
-    const bool valid = m < nT;
     const int x = m * T + u;
+    const bool valid = m < nT && x < L;  // (+1) tilings: last class columns partly unused
     const int RL = (L + kSeg - 1) / kSeg;
     const int y0 = min(L, seg * RL), y1 = min(L, y0 + RL);
     int r[8], s1[8], vprev[8];

@@ -57,14 +57,13 @@ extern "C" int rsos_width_noalloc(const rsos_params* params, const uint32_t* pla
     int rc = rsos_required_bytes(params, &job_bytes);
     if (rc) return rc;
     if (params->surfaces < 2) return RSOS_EINVAL;  // the plain path keeps absolute heights
-    // layout tile edge: row-major site records (1) for the (+1) tilings
-    const int T = params->tiling == 1 ? 1 : (params->tile_x == 0 ? 8 : params->tile_x);
+    const int T = params->tile_x == 0 ? 8 : params->tile_x;
     rsos::JobDev J{};
     J.planes = const_cast<uint32_t*>(planes);
     J.h00 = const_cast<int64_t*>(h00);
     J.L = params->L;
     J.T = T;
-    J.nT = params->L / T;
+    J.nT = params->tiling == 1 ? rsos::gen_classes(params->L, T) : params->L / T;  // class columns per row
     J.NW = (params->surfaces + 31) / 32;
     J.NWP = J.NW;
     J.N = params->N;

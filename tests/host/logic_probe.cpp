@@ -205,16 +205,20 @@ long long probe_gen_div_check(void)
 }
 
 // For every origin of one period, set q, tile and lane-word group: every
-// non-corner window slot's word offset (gen_window_word + plane b + word w)
-// is in range and is the word of site ((ox + u0 + ii - 1) mod L,
-// (oy + v0 + jj - 1) mod L); the interior slots of the four sets cover every
-// site exactly once; the slot gen_locate_origin_site names is site (0,0).
-// Returns the number of failures; *n_checked = checks made.
+// non-corner window slot's word offset, walked as the kernel walks it
+// (columns by gen_col / gen_col_next, rows by gen_row_words, plus plane b and
+// word w), is in range and is the word of site ((ox + u0 + ii - 1) mod L,
+// (oy + v0 + jj - 1) mod L) in the class-interleaved layout
+// (((y T + x mod T) nT + x div T) B + b) NW + w with nT = ceil(L / T); the
+// interior slots of the four sets cover every site exactly once; the slot
+// gen_locate_origin_site names is site (0,0).  Returns the number of
+// failures; *n_checked = checks made.
 long long probe_gen_window_check(int L, int Tx, int Ty, int NW, int B, int NWT, long long* n_checked)
 {
     const rsos::GenTiling G = rsos::gen_tiling(L, Tx, Ty);
+    const int T = Tx, nT = rsos::gen_classes(L, Tx);
     const size_t rec_words = (size_t)B * NW;
-    const long long total = (long long)B * L * L * NW;
+    const long long total = (long long)B * L * T * nT * NW;
     const int px = rsos::gen_period(L, Tx), py = rsos::gen_period(L, Ty);
     std::vector<int> cover((size_t)L * L);
     long long bad = 0, n = 0;
@@ -228,8 +232,10 @@ long long probe_gen_window_check(int L, int Tx, int Ty, int NW, int B, int NWT, 
                         int u0, sw, v0, sh;
                         rsos::gen_half(G.x, tx, q & 1, u0, sw);
                         rsos::gen_half(G.y, ty, q >> 1, v0, sh);
-                        for (int jj = 0; jj < sh + 2; ++jj)
-                            for (int ii = 0; ii < sw + 2; ++ii) {
+                        rsos::GenCol col = rsos::gen_col(L, T, ox + u0 - 1);
+                        for (int ii = 0; ii < sw + 2; ++ii) {
+                            const size_t cw = rsos::gen_col_words(col, nT, rec_words);
+                            for (int jj = 0; jj < sh + 2; ++jj) {
                                 const bool edge_row = jj == 0 || jj == sh + 1, edge_col = ii == 0 || ii == sw + 1;
                                 if (edge_row && edge_col) continue;
                                 const int x = ((ox + u0 + ii - 1) % L + L) % L;
@@ -241,17 +247,19 @@ long long probe_gen_window_check(int L, int Tx, int Ty, int NW, int B, int NWT, 
                                     const bool named = q == o.q && tx == o.tx && ty == o.ty && k == o.k;
                                     bad += is00 != named;
                                 }
-                                for (int w0 = 0; w0 + NWT <= NW; w0 += NWT) {
-                                    const size_t base = rsos::gen_window_word(L, rec_words, ox, oy, u0, v0, ii, jj, w0);
+                                const size_t rw = rsos::gen_row_words(L, T, nT, rec_words, oy + v0 + jj - 1);
+                                const long long rec = ((long long)y * T + x % T) * nT + x / T;
+                                for (int w0 = 0; w0 + NWT <= NW; w0 += NWT)
                                     for (int b = 0; b < B; ++b)
                                         for (int w = 0; w < NWT; ++w) {
-                                            const long long want = (((long long)y * L + x) * B + b) * NW + w0 + w;
-                                            const long long got = (long long)base + (long long)b * NW + w;
+                                            const long long want = (rec * B + b) * NW + w0 + w;
+                                            const long long got = (long long)(rw + cw) + w0 + (long long)b * NW + w;
                                             bad += (got != want || got < 0 || got >= total) ? 1 : 0;
                                             ++n;
                                         }
-                                }
                             }
+                            rsos::gen_col_next(col, L, T);
+                        }
                     }
             for (int v : cover) bad += v != 1;
         }

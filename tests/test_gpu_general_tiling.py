@@ -173,7 +173,8 @@ def test_noalloc_width_on_general_layout():
     nbytes = R.rsos_required_bytes(p)
     buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
     base = (buf.data_ptr() + 255) // 256 * 256
-    h00_off = (2 * L * L * 2 * 4 + 255) // 256 * 256
+    # planes: L rows of 6 ceil(L / 6) 16-byte records (class-interleaved, padded)
+    h00_off = (2 * L * 6 * ((L + 5) // 6) * 2 * 4 + 255) // 256 * 256
     out = torch.zeros(S * 4, dtype=torch.int64, device="cuda")
     h = R.rsos_init(p, dev_buf=base, dev_bytes=nbytes)
     try:
