@@ -8,6 +8,8 @@
 // selection is Eq. 6 on bit-sliced words; the stream is the regular one with
 // a = the sub-tile's own area: 2a selections per activation, site index
 // k = floor(u a / 2^16) of a 16-bit u, kx = k mod w, ky = k div w.
+#include <mutex>
+
 #include "rsos_general.cuh"
 #include "rsos_launch.h"
 
@@ -128,6 +130,19 @@ __global__ void __launch_bounds__(256) general_phase_kernel(JobDev J, GenTiling 
         general_activate<N, WT, false>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, -1);
 }
 
+constexpr size_t kMaxDynamicSmem = 227 * 1024;  // largest dynamic shared memory of a block
+
+// Allows general_phase_kernel<N, WT> the largest dynamic shared memory, once
+// (thread-safe static initialisation).
+template <int N, typename WT>
+cudaError_t general_allow_smem()
+{
+    static const cudaError_t e = cudaFuncSetAttribute(general_phase_kernel<N, WT>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)kMaxDynamicSmem);
+    return e;
+}
+
 // Threads per block that keep the most threads resident per SM for windows
 // of per_thread bytes (shared memory is the limit; ties go to larger blocks).
 template <int N, typename WT>
@@ -137,11 +152,6 @@ int general_block_threads(size_t per_thread, size_t smem_cap)
     for (int n = 32; n <= 256; n += 32) {
         const size_t smem = per_thread * (size_t)n;
         if (smem > smem_cap) break;
-        if (cudaFuncSetAttribute(general_phase_kernel<N, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess) {
-            (void)cudaGetLastError();
-            break;
-        }
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, general_phase_kernel<N, WT>, n, smem) !=
             cudaSuccess) {
@@ -165,20 +175,28 @@ cudaError_t launch_general_t(const JobDev& J, const GenTiling& G, uint32_t t, in
     const size_t wbytes = (size_t)B * sizeof(WT);  // one window slot
     const size_t pt_narrow = gen_narrow_window_slots(G) * wbytes;
     const size_t pt_wide = (size_t)(G.max_w + 2) * (G.max_h + 2) * wbytes;
-    if (pt_wide * 8 > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (pt_wide * 8 > kMaxDynamicSmem) return cudaErrorInvalidConfiguration;
+    const cudaError_t allowed = general_allow_smem<N, WT>();
+    if (allowed != cudaSuccess) return allowed;
     const size_t cap = smem_budget < pt_narrow * 32 ? pt_narrow * 32 : smem_budget;
-    // block size per (window bytes, budget), remembered for a few windows
+    // block size per (window bytes, budget), remembered for a few windows;
+    // handles on different host threads may launch concurrently
     struct Plan {
         size_t per_thread, cap;
         int n;
     };
     static Plan plans[8] = {};
     static int n_plans = 0;
+    static std::mutex plans_mu;
     int n = 0;
-    for (int k = 0; k < n_plans; ++k)
-        if (plans[k].per_thread == pt_narrow && plans[k].cap == cap) n = plans[k].n;
+    {
+        std::lock_guard<std::mutex> lock(plans_mu);
+        for (int k = 0; k < n_plans; ++k)
+            if (plans[k].per_thread == pt_narrow && plans[k].cap == cap) n = plans[k].n;
+    }
     if (n == 0) {
-        n = general_block_threads<N, WT>(pt_narrow, cap > 227 * 1024 ? 227 * 1024 : cap);
+        n = general_block_threads<N, WT>(pt_narrow, cap > kMaxDynamicSmem ? kMaxDynamicSmem : cap);
+        std::lock_guard<std::mutex> lock(plans_mu);
         if (n_plans < 8) plans[n_plans++] = Plan{pt_narrow, cap, n};
     }
     GenLaunch P;
@@ -186,9 +204,6 @@ cudaError_t launch_general_t(const JobDev& J, const GenTiling& G, uint32_t t, in
     long long blocks = 0;
     gen_plan_launch(G, J.NWP, wbytes, n, P, smem, blocks);
     if (blocks == 0) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(general_phase_kernel<N, WT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     general_phase_kernel<N, WT><<<(unsigned)blocks, (unsigned)n, smem, s>>>(J, G, P, t, p, q, ox, oy, o);
     *n_launches = 1;
     return cudaGetLastError();

@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(512) plain_phase_kernel(JobDev J, uint32_t t, 
     activate_subtile_plain<SX>(J, sm, tid, nthr, tx, ty, t, p, q, ox, oy);
 }
 
+// Largest dynamic shared memory of one block (227 KB).
+constexpr size_t kMaxDynamicSmem = 227 * 1024;
+
 inline int pick_threads(size_t per_thread, size_t smem_budget, long long total)
 {
     long long n = (long long)(smem_budget / per_thread) / 32 * 32;
@@ -57,13 +60,11 @@ cudaError_t launch_phase_t(const JobDev& J, uint32_t t, int p, int q, int ox, in
     const long long total = (long long)J.nT * J.nT * J.NWP;
     const int nthr = pick_threads(per_thread, smem_budget, total);
     const size_t smem = per_thread * nthr;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(phase_kernel<N, WT, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    // Allow the largest dynamic shared memory once (thread-safe static
+    // initialisation; handles on different host threads launch concurrently).
+    static const cudaError_t allowed = cudaFuncSetAttribute(
+        phase_kernel<N, WT, SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynamicSmem);
+    if (allowed != cudaSuccess) return allowed;
     const long long blocks = (total + nthr - 1) / nthr;
     phase_kernel<N, WT, SX><<<(unsigned)blocks, nthr, smem, s>>>(J, t, p, q, ox, oy, o);
     return cudaGetLastError();
@@ -100,13 +101,9 @@ cudaError_t launch_plain_sx(const JobDev& J, uint32_t t, int p, int q, int ox, i
     const long long total = (long long)J.nT * J.nT;
     const int nthr = pick_threads(per_thread, smem_budget, total);
     const size_t smem = per_thread * nthr;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(plain_phase_kernel<SX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static const cudaError_t allowed = cudaFuncSetAttribute(
+        plain_phase_kernel<SX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynamicSmem);
+    if (allowed != cudaSuccess) return allowed;
     const long long blocks = (total + nthr - 1) / nthr;
     plain_phase_kernel<SX><<<(unsigned)blocks, nthr, smem, s>>>(J, t, p, q, ox, oy);
     return cudaGetLastError();
