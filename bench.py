@@ -261,6 +261,14 @@ def run_gpu(args):
     if rank != 0:
         return
     cpu = cpu_baseline(L, W["N"], W["tile"], seed, tiling=W["tiling"]) if world == 1 else None
+    # Integer-pipe side of the roofline: measured lop3 / mad.lo lane rates and
+    # Philox blocks/s.  A 64-lane selection draws 1/8 site block and 2/4 mask
+    # blocks; each lane sees two selections per expected attempt.
+    philox_per_attempt = (1.0 / 8 + 2.0 / 4) * 2.0 / 64
+    int_peaks = {"lop3_lane_ops_per_s": R.rsos_peak_int(0, 4096, stream),
+                 "imad_lane_ops_per_s": R.rsos_peak_int(1, 4096, stream),
+                 "philox_blocks_per_s": R.rsos_peak_int(2, 512, stream)}
+    int_peaks["philox_bound_attempts_per_s"] = int_peaks["philox_blocks_per_s"] / philox_per_attempt
     lanes_note = f"inputs larger than L2 ({L * L * S * rsos_bits(W['N']) / 8 / 2 ** 20:.0f} MiB lattice per job)"
     line = {
         "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
@@ -275,6 +283,7 @@ def run_gpu(args):
                      "sweeps_per_launch": n_kernel_sweeps / n_launch,
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
         "cpu_baseline": cpu,
+        "int_peaks": int_peaks,
         "clocks": clk,
         "gpu_launches": launches_per_job * args.steps,
         "w2_final_mean": float(sum(w2[-1]) / len(w2[-1])),

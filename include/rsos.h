@@ -254,6 +254,18 @@ int rsos_free(rsos_handle* h);
 /* Static description of a status code. */
 const char* rsos_strerror(int status);
 
+/* Integer throughput of this GPU, measured (no counterpart in the paper: the
+ * integer-pipe roofline of the sweep).  kind 0: 3-input logic (lop3, the
+ * ALU pipe that runs the bit-sliced Eq. 6 test); 1: 32-bit multiply-add
+ * (mad.lo, the FMA pipe of Philox and the site mapping); 2: Philox-4x32-10
+ * blocks with precomputed round keys.  Runs `iters` iterations per thread of
+ * a fixed instruction chain on 2048 threads per SM after a short warm-up,
+ * timed with CUDA events on stream.  *per_s = 32-bit lane operations
+ * (kinds 0, 1) or Philox blocks (kind 2) per second.  Synchronises the
+ * stream.  RSOS_EINVAL for a bad kind, iters outside 1..2^30 or a NULL
+ * per_s; RSOS_ECUDA on a CUDA error. */
+int rsos_peak_int(int32_t kind, int64_t iters, double* per_s, void* stream);
+
 /* CUDA error code behind the last RSOS_ECUDA of the handle (0 if none); with
  * h == NULL, the CUDA error of the last failed rsos_init on this thread. */
 int rsos_last_cuda_error(const rsos_handle* h);

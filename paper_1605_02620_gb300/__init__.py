@@ -113,6 +113,7 @@ def _load():
             "rsos_batch_poll": [vp, P(i32), i32, P(i32)],
             "rsos_batch_job": [vp, i32, P(vp)],
             "rsos_batch_free": [vp],
+            "rsos_peak_int": [i32, i64, P(ctypes.c_double), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -305,6 +306,14 @@ def rsos_advance(handles, targets, stream=None) -> None:
     rc = _load().rsos_advance(arr, _p(tg, ctypes.c_int64), n, _stream(stream))
     if rc != RSOS_OK:
         raise RsosError(rc, "rsos_advance", _load().rsos_last_cuda_error(None) if rc == RSOS_ECUDA else 0)
+
+
+def rsos_peak_int(kind: int, iters: int = 4096, stream=None) -> float:
+    """Measured integer throughput: kind 0 lop3 lane-ops/s, 1 mad.lo
+    lane-ops/s, 2 Philox-4x32-10 blocks/s."""
+    out = ctypes.c_double()
+    _check(_load().rsos_peak_int(int(kind), int(iters), ctypes.byref(out), _stream(stream)), "rsos_peak_int")
+    return out.value
 
 
 def rsos_launches(h) -> int:

@@ -84,3 +84,12 @@ def test_general_tiling_params_validated_without_gpu():
     # regular tilings keep their rules: 6 x 10 is not a regular tile
     with pytest.raises(R.RsosError):
         R.rsos_required_bytes(R.rsos_params(**dict(ok, tiling=0)))
+
+
+def test_peak_probe_rejects_bad_arguments_without_gpu():
+    import paper_1605_02620_gb300 as R
+    import pytest
+    for kind, iters in [(3, 10), (-1, 10), (0, 0), (1, -5), (2, 1 << 31)]:
+        with pytest.raises(R.RsosError) as e:
+            R.rsos_peak_int(kind, iters)
+        assert e.value.status == -1
