@@ -254,6 +254,17 @@ int rsos_free(rsos_handle* h);
 /* Static description of a status code. */
 const char* rsos_strerror(int status);
 
+/* 1 if this library is the bounds-checked build (RSOS_CHECKED: every record
+ * a sweep kernel stages or writes back is tested against the lattice and
+ * every shared-memory record against the block's dynamic shared memory; a
+ * failed test is counted and the access skipped), else 0. */
+int rsos_checked_build(void);
+
+/* Out-of-range accesses counted for this job since rsos_init (always 0 in
+ * the normal build, which does not test).  Synchronises the stream.
+ * RSOS_EINVAL for NULL arguments, RSOS_ECUDA on a CUDA error. */
+int rsos_bounds_errors(rsos_handle* h, uint32_t* count, void* stream);
+
 /* Integer throughput of this GPU, measured (no counterpart in the paper: the
  * integer-pipe roofline of the sweep).  kind 0: 3-input logic (lop3, the
  * ALU pipe that runs the bit-sliced Eq. 6 test); 1: 32-bit multiply-add

@@ -38,7 +38,9 @@ RSOS_EBUSY = -6
 RSOS_ERANGE = -7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_build", "librsos.so")
+# RSOS_CHECKED=1 loads the bounds-checked build (built on first use).
+_CHECKED = os.environ.get("RSOS_CHECKED", "0") == "1"
+_LIB_PATH = os.path.join(_HERE, "_build_checked" if _CHECKED else "_build", "librsos.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -81,7 +83,7 @@ def _load():
             return _lib
         if not os.path.exists(_LIB_PATH):
             from . import build as _build
-            _build.build()
+            _build.build(checked=_CHECKED)
         lib = ctypes.CDLL(_LIB_PATH)
         vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
         P = ctypes.POINTER
@@ -114,6 +116,8 @@ def _load():
             "rsos_batch_job": [vp, i32, P(vp)],
             "rsos_batch_free": [vp],
             "rsos_peak_int": [i32, i64, P(ctypes.c_double), vp],
+            "rsos_checked_build": [],
+            "rsos_bounds_errors": [vp, P(ctypes.c_uint32), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -314,6 +318,18 @@ def rsos_peak_int(kind: int, iters: int = 4096, stream=None) -> float:
     out = ctypes.c_double()
     _check(_load().rsos_peak_int(int(kind), int(iters), ctypes.byref(out), _stream(stream)), "rsos_peak_int")
     return out.value
+
+
+def rsos_checked_build() -> bool:
+    """True if the loaded library is the bounds-checked build."""
+    return _load().rsos_checked_build() == 1
+
+
+def rsos_bounds_errors(h, stream=None) -> int:
+    """Out-of-range accesses counted for the job (checked build; else 0)."""
+    n = ctypes.c_uint32()
+    _check(_load().rsos_bounds_errors(h, ctypes.byref(n), _stream(stream)), "rsos_bounds_errors")
+    return n.value
 
 
 def rsos_launches(h) -> int:

@@ -19,6 +19,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librsos.so")
+# bounds-checked build (-DRSOS_CHECKED): same sources, its own objects
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "librsos.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -44,8 +47,13 @@ def _compile(nvcc: str, src: str, obj: str, extra) -> None:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}\n{r.stdout}")
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if needed) and return the path of librsos.so."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile (if needed) and return the path of librsos.so; checked=True
+    builds the bounds-checked library (RSOS_CHECKED) in _build_checked/."""
+    BUILD = BUILD_CHECKED if checked else globals()["BUILD"]
+    LIB = LIB_CHECKED if checked else globals()["LIB"]
+    if checked:
+        extra_flags = (*extra_flags, "-DRSOS_CHECKED")
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))

@@ -67,7 +67,7 @@ constexpr int kRecWords = 8;
 thread_local int g_init_cuda_err = 0;
 
 struct Layout {
-    size_t planes, h00, row0, partial, rec, persist, total;
+    size_t planes, h00, row0, partial, rec, persist, check, total;
     int ncb, S_pad, B, NW, T, cap;
     int nTc;    // class columns per row of the layout
     int CW, K;  // persistent engine: tiles per block, chunks per tile row
@@ -207,7 +207,8 @@ Layout layout_of(const rsos_params* p)
         l.K = (nT + l.CW - 1) / l.CW;
         l.persist = align256((size_t)4 * nT * 8) + 256;
     }
-    l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec + l.persist;
+    l.check = 256;  // checked build: out-of-range access counter (last region)
+    l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec + l.persist + l.check;
     return l;
 }
 
@@ -555,6 +556,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     J.seed_lo = (uint32_t)params->seed;
     J.seed_hi = (uint32_t)(params->seed >> 32);
     J.rk = rsos::philox_round_keys(J.seed_lo, J.seed_hi);
+    J.bounds_err = reinterpret_cast<uint32_t*>(h->base + (l.total - l.check));
     cudaError_t e = cudaSuccess;
     if (l.persist_on) {
         e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, params->phase_lag, &h->plan);
@@ -564,6 +566,7 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     }
     // Flat initial condition (section II): planes and h00 zero.
     if (e == cudaSuccess) e = rsos::launch_zero(h->base, l.planes + l.h00, as_stream(stream));
+    if (e == cudaSuccess) e = rsos::launch_zero(J.bounds_err, l.check, as_stream(stream));
     if (e != cudaSuccess) {
         g_init_cuda_err = (int)e;
         (void)cudaGetLastError();
@@ -602,6 +605,24 @@ int rsos_sweep(rsos_handle* h, int64_t n_sweeps, void* stream)
         if (rc) return rc;
     }
     return RSOS_OK;
+}
+
+int rsos_checked_build(void)
+{
+#if defined(RSOS_CHECKED)
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int rsos_bounds_errors(rsos_handle* h, uint32_t* count, void* stream)
+{
+    if (!h || !count) return RSOS_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(count, h->J.bounds_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return fail_cuda(h, e);
 }
 
 int rsos_selftest_timeout(rsos_handle* h, int64_t budget_ns, void* stream)

@@ -34,6 +34,7 @@ struct JobDev {
     int32_t phase_order;
     uint32_t seed_lo, seed_hi;
     RoundKeys rk;       // Philox round keys of the seed
+    uint32_t* bounds_err;  // checked build: count of out-of-range accesses (nullable)
 };
 
 // Where site (0,0) lies in the tiling of one sweep.
@@ -115,6 +116,44 @@ RSOS_HD void window_index(const JobDev& J, int tx, int ty, int qx, int qy, int o
 }
 
 #if defined(__CUDACC__)
+
+// Checked build (RSOS_CHECKED): every record a sweep kernel stages or writes
+// back is tested against the lattice, and every shared-memory record it
+// touches against the block's dynamic shared memory.  A failed test counts
+// in *J.bounds_err and the access is skipped (no trap: the context stays
+// usable).  In the normal build both tests are the constant true.
+#if defined(RSOS_CHECKED)
+__device__ __forceinline__ void count_bounds_error(const JobDev& J)
+{
+    if (J.bounds_err) atomicAdd(J.bounds_err, 1u);
+}
+
+// words 32-bit words from p lie inside the multisurface lattice.
+__device__ __forceinline__ bool check_global(const JobDev& J, const uint32_t* p, size_t words)
+{
+    const size_t total = (size_t)J.B * (size_t)J.L * (size_t)J.T * (size_t)J.nT * (size_t)J.NW;
+    const bool ok = p >= J.planes && (size_t)(p - J.planes) + words <= total;
+    if (!ok) count_bounds_error(J);
+    return ok;
+}
+
+// bytes bytes from p lie inside the block's dynamic shared memory.
+__device__ __forceinline__ bool check_shared(const JobDev& J, const void* p, size_t bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned dyn = 0;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    const bool ok = c >= smem_raw && (size_t)(c - smem_raw) + bytes <= (size_t)dyn;
+    if (!ok) count_bounds_error(J);
+    return ok;
+}
+#define RSOS_CHECK_GLOBAL(J, p, words) ::rsos::check_global((J), (p), (words))
+#define RSOS_CHECK_SHARED(J, p, bytes) ::rsos::check_shared((J), (p), (bytes))
+#else
+#define RSOS_CHECK_GLOBAL(J, p, words) true
+#define RSOS_CHECK_SHARED(J, p, bytes) true
+#endif
 
 template <typename WT>
 __device__ __forceinline__ WT mask_word(const U4& lo, const U4& hi, int r);
@@ -293,6 +332,9 @@ __device__ __forceinline__ void select_subtile(const JobDev& J, WT* __restrict__
                 const int s = (ky + 1) * WW + kx + 1;
                 WT* base = sm + ((size_t)s * nthr + tid) * B;
                 const size_t rs = (size_t)nthr * B;  // one slot
+                if (!RSOS_CHECK_SHARED(J, base - WW * rs, sizeof(WT) * B) ||
+                    !RSOS_CHECK_SHARED(J, base + WW * rs, sizeof(WT) * B))
+                    continue;
                 WT x[B], e[B], w[B], n[B], so[B];
                 load_rec<B, WT>(base, x);
                 load_rec<B, WT>(base + rs, e);
@@ -345,6 +387,8 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             const int s = jj * WW + ii;
             WT* slot = sm + ((size_t)s * nthr + tid) * B;
             const uint32_t* src = J.planes + wi.row[jj] + wi.col[ii];
+            if (!RSOS_CHECK_GLOBAL(J, src, (size_t)(B - 1) * J.NW + NWT) || !RSOS_CHECK_SHARED(J, slot, sizeof(WT) * B))
+                continue;
             if (ASYNC) {
                 stage_record_async<WT, B>(slot, src, J.NW, whole_record);
             } else {
@@ -366,6 +410,8 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             const int s = jj * WW + ii;
             const WT* slot = sm + ((size_t)s * nthr + tid) * B;
             uint32_t* dst = J.planes + wi.row[jj] + wi.col[ii];
+            if (!RSOS_CHECK_GLOBAL(J, dst, (size_t)(B - 1) * J.NW + NWT) || !RSOS_CHECK_SHARED(J, slot, sizeof(WT) * B))
+                continue;
             if (B * sizeof(WT) == 16 && whole_record) {
                 WT v[B];
                 load_rec<B, WT>(slot, v);

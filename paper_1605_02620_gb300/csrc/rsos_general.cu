@@ -44,6 +44,9 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
         for (int jj = edge_col ? 1 : 0; jj < (edge_col ? sh + 1 : sh + 2); ++jj) {
             WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
             const size_t rw = gen_row_words(L, J.T, J.nT, rec_words, oy + v0 + jj - 1);
+            if (!RSOS_CHECK_GLOBAL(J, J.planes + rw + cw, (size_t)(B - 1) * J.NW + NWT) ||
+                !RSOS_CHECK_SHARED(J, slot, sizeof(WT) * B))
+                continue;
             stage_record_async<WT, B>(slot, J.planes + rw + cw, J.NW, whole_record);
         }
         gen_col_next(col, L, J.T);
@@ -76,6 +79,9 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
                 const uint32_t kx = k - ky * (uint32_t)sw;
                 const int s = ((int)ky + 1) * WW + (int)kx + 1;
                 WT* base = sm + ((size_t)s * nthr + tid) * B;
+                if (!RSOS_CHECK_SHARED(J, base - (size_t)WW * rs, sizeof(WT) * B) ||
+                    !RSOS_CHECK_SHARED(J, base + (size_t)WW * rs, sizeof(WT) * B))
+                    continue;
                 WT x[B], e[B], w[B], n[B], so[B];
                 load_rec<B, WT>(base, x);
                 load_rec<B, WT>(base + rs, e);
@@ -98,6 +104,8 @@ __device__ __forceinline__ void general_activate(const JobDev& J, const GenTilin
         for (int jj = 1; jj <= sh; ++jj) {
             const WT* slot = sm + ((size_t)(jj * WW + ii) * nthr + tid) * B;
             uint32_t* dst = J.planes + gen_row_words(L, J.T, J.nT, rec_words, oy + v0 + jj - 1) + cw;
+            if (!RSOS_CHECK_GLOBAL(J, dst, (size_t)(B - 1) * J.NW + NWT) || !RSOS_CHECK_SHARED(J, slot, sizeof(WT) * B))
+                continue;
             WT v[B];
             load_rec<B, WT>(slot, v);
             if (B * sizeof(WT) == 16 && whole_record) {

@@ -93,3 +93,11 @@ def test_peak_probe_rejects_bad_arguments_without_gpu():
         with pytest.raises(R.RsosError) as e:
             R.rsos_peak_int(kind, iters)
         assert e.value.status == -1
+
+
+def test_normal_build_is_not_the_checked_one_without_gpu():
+    import paper_1605_02620_gb300 as R
+    import pytest
+    assert R.rsos_checked_build() is False
+    with pytest.raises(R.RsosError):
+        R.rsos_bounds_errors(None)
