@@ -166,7 +166,8 @@ def test_batch_and_advance_run_general_jobs():
 
 
 def test_noalloc_width_on_general_layout():
-    """rsos_width_noalloc reads the row-major records of a (+1) tiling."""
+    """rsos_width_noalloc reads the padded class-interleaved records of a (+1)
+    tiling."""
     import torch
     L, S = 64, 64
     p = R.rsos_params(L=L, N=1, surfaces=S, tile=(6, 10), seed=21, series_capacity=4, tiling=1)

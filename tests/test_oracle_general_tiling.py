@@ -2,7 +2,8 @@
 pinned to what the paper and the mathematics fix.
 
 * With T even and dividing L a (+1) tiling is the regular tiling of section
-  II, so both sweeps must give the same heights, bit for bit.
+  II, so both sweeps must give the same heights, bit for bit; so is a single
+  (T + 1)-wide tile per axis on L = T + 1, reached through the (+1) rule.
 * The halves of every axis partition the lattice and the halves of one set
   never touch, which is what lets a set be updated in parallel (section II).
 * N -> infinity (random deposition): a site of a sub-tile of a sites receives
@@ -147,3 +148,16 @@ def test_rejects_impossible_tilings():
         O.sweeps(O.Params(L=10, N=1, Tx=7, Ty=2, tiling=1), h, [0], 0, 1)
     with pytest.raises(ValueError):  # sub-tiles need at least one site
         O.sweeps(O.Params(L=10, N=1, Tx=1, Ty=2, tiling=1), h, [0], 0, 1)
+
+
+@pytest.mark.parametrize("L,N", [(4, 1), (6, 2), (8, 3)])
+def test_single_wide_tile_is_the_regular_tiling(L, N):
+    """L = T + 1 with T + 1 even: one tile of L sites per axis, halved into
+    L/2 + L/2, and the origin uniform over L — the regular tiling with edge L,
+    reached through the (+1) rule (r = 1), bit for bit."""
+    lanes = [0, 9, 33]
+    a = O.flat(L, len(lanes))
+    b = O.flat(L, len(lanes))
+    O.sweeps(O.Params(L=L, N=N, Tx=L, Ty=L, seed=L), a, lanes, 0, 40)
+    O.sweeps(O.Params(L=L, N=N, Tx=L - 1, Ty=L - 1, seed=L, tiling=1), b, lanes, 0, 40)
+    assert np.array_equal(a, b)
