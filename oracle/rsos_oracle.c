@@ -19,8 +19,8 @@
  *     decomposition check (section III.C), whose tiles are T or T + 1 wide;
  *   - multisurface coding (section II): the surfaces ("lanes") of one job share
  *     the sequence of selected sites; each lane takes part in a selection only
- *     if its own random mask bit is set ("updating only half of the selected
- *     lattice sites in each attempt");
+ *     if its own random mask bit is set, so a selected site is updated in
+ *     about half of the surfaces;
  *   - a true random-sequential (RS) reference dynamics: L^2 attempts at
  *     uniformly chosen sites per Monte-Carlo step;
  *   - exact sums of h and h^2 per lane, from which the squared interface width
