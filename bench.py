@@ -125,18 +125,23 @@ class ClockSampler:
 
 def dist_setup(n_gpus: int):
     """Ranks from the torchrun environment; one process group for the
-    timing reductions (NCCL with GPUs, gloo on a host without)."""
+    timing reductions (NCCL with GPUs, gloo on a host without).  A rank that
+    dies or never arrives ends the others' next collective with an error after
+    RSOS_DIST_TIMEOUT_S seconds (default 600) instead of a hang."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        import torch.distributed as dist
+        import datetime
+
         import torch
+        import torch.distributed as dist
+        timeout = datetime.timedelta(seconds=float(os.environ.get("RSOS_DIST_TIMEOUT_S", "600")))
         if torch.cuda.is_available():
             torch.cuda.set_device(local)
-            dist.init_process_group("nccl")
+            dist.init_process_group("nccl", timeout=timeout)
         else:
-            dist.init_process_group("gloo")
+            dist.init_process_group("gloo", timeout=timeout)
     return world, rank, local
 
 

@@ -9,6 +9,14 @@ overlaps on the GPU).  Between epochs it retires jobs that reached t_max
 queued requests first-come first-served while their device memory fits the
 budget.  Each job's result is bit-identical to running it alone.
 
+Faults stay with the jobs they concern: a request larger than the whole
+budget is rejected, a request whose job cannot be created (rsos_init raises)
+fails alone, a request may be cancelled at a given time (queued: dropped;
+resident: its memory is released at the next epoch boundary), and if an
+epoch's rsos_advance raises, the jobs resident in that epoch are released and
+reported failed while the queue carries on.  Every request ends with a
+status: done, rejected, cancelled or failed.
+
 Everything that computes runs in the library's kernels; this module only
 decides which jobs advance how far in each epoch.
 """
@@ -32,17 +40,20 @@ class Request:
     surfaces: int = 64
     arrival: float = 0.0
     rid: int = 0
+    cancel_at: float | None = None  # cancelled by the client at this time (None: never)
 
 
 @dataclass
 class Result:
     rid: int
     arrival: float
-    admitted: float
+    admitted: float | None  # None: never resident
     finished: float
-    sum_h: np.ndarray
-    sum_h2: np.ndarray
-    w2: np.ndarray
+    sum_h: np.ndarray | None  # None unless status == "done"
+    sum_h2: np.ndarray | None
+    w2: np.ndarray | None
+    status: str = "done"  # done, rejected, cancelled, failed
+    error: str = ""
 
     @property
     def latency(self) -> float:
@@ -68,9 +79,13 @@ class Report:
     offered_attempts_per_s: float = 0.0
 
     def summary(self) -> dict:
-        lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
+        done = [r for r in self.results if r.status == "done"]
+        lat = np.array([r.latency for r in done]) if done else np.zeros(1)
         return {
-            "jobs": len(self.results),
+            "jobs": len(done),
+            "rejected": sum(r.status == "rejected" for r in self.results),
+            "cancelled": sum(r.status == "cancelled" for r in self.results),
+            "failed": sum(r.status == "failed" for r in self.results),
             "wall_s": self.wall_s,
             "attempts_per_s": self.attempts / self.wall_s if self.wall_s > 0 else 0.0,
             "attempts_per_busy_s": self.attempts / self.gpu_busy_s if self.gpu_busy_s > 0 else 0.0,
@@ -113,23 +128,64 @@ class Server:
         used = 0
         nxt = 0
         t_start = clock()
+
+        def end(req, admitted, status, error=""):
+            rep.results.append(Result(req.rid, req.arrival, admitted, clock() - t_start, None, None, None,
+                                      status, error))
+
+        def release(a):
+            nonlocal used
+            try:
+                rsos_free(a.handle)
+            finally:
+                used -= a.nbytes
+
         while nxt < len(reqs) or queue or active:
             now = clock() - t_start
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 queue.append(reqs[nxt])
                 nxt += 1
+            # cancellations: queued requests leave the queue, resident jobs
+            # release their memory at this epoch boundary
+            for r in [r for r in queue if r.cancel_at is not None and r.cancel_at <= now]:
+                queue.remove(r)
+                end(r, None, "cancelled")
+            keep = []
+            for a in active:
+                if a.req.cancel_at is not None and a.req.cancel_at <= now:
+                    release(a)
+                    end(a.req, a.admitted, "cancelled")
+                else:
+                    keep.append(a)
+            active = keep
             # admit first-come first-served while memory allows
             while queue:
                 r = queue[0]
-                p = self._params(r)
-                nbytes = rsos_required_bytes(p)
+                try:
+                    p = self._params(r)
+                    nbytes = rsos_required_bytes(p)
+                except RsosError as e:
+                    queue.pop(0)
+                    end(r, None, "rejected", str(e))
+                    continue
                 if nbytes > self.hbm_budget:
-                    raise RsosError(-2, f"request {r.rid} needs {nbytes} bytes, more than the budget")
+                    queue.pop(0)
+                    end(r, None, "rejected", f"needs {nbytes} bytes, more than the budget {self.hbm_budget}")
+                    continue
                 if used + nbytes > self.hbm_budget:
                     break
                 queue.pop(0)
-                h = rsos_init(p, stream=self.stream)
-                rsos_schedule(h, [r.t_max])
+                try:
+                    h = rsos_init(p, stream=self.stream)
+                except RsosError as e:
+                    end(r, None, "failed", str(e))
+                    continue
+                try:
+                    rsos_schedule(h, [r.t_max])
+                except RsosError as e:
+                    rsos_free(h)
+                    end(r, now, "failed", str(e))
+                    continue
                 active.append(_Active(r, h, nbytes, now))
                 used += nbytes
             rep.max_active = max(rep.max_active, len(active))
@@ -148,7 +204,18 @@ class Server:
                 targets.append(tt)
                 planned += unit * (tt - t)
             e0 = clock()
-            rsos_advance([a.handle for a in active], targets, self.stream)
+            try:
+                rsos_advance([a.handle for a in active], targets, self.stream)
+            except RsosError as e:
+                # the epoch's jobs are in an unknown state: release them all
+                for a in active:
+                    try:
+                        release(a)
+                    except RsosError:
+                        pass
+                    end(a.req, a.admitted, "failed", str(e))
+                active = []
+                continue
             dt = clock() - e0
             rep.gpu_busy_s += dt
             rep.attempts += planned
@@ -160,8 +227,7 @@ class Server:
             for a, tt in zip(active, targets):
                 if tt >= a.req.t_max:
                     ts, s1, s2, w2 = rsos_read_series(a.handle, a.req.surfaces, 2, self.stream)
-                    rsos_free(a.handle)
-                    used -= a.nbytes
+                    release(a)
                     rep.results.append(Result(a.req.rid, a.req.arrival, a.admitted, clock() - t_start,
                                               s1[-1].copy(), s2[-1].copy(), w2[-1].copy()))
                 else:

@@ -45,6 +45,19 @@ void probe_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out)
     out[0] = r.x; out[1] = r.y; out[2] = r.z; out[3] = r.w;
 }
 
+// n consecutive blocks from counter ctr0 (words 0-1 as one 64-bit count),
+// with the round keys precomputed as the sweep kernels use them.
+void probe_philox_bulk(const uint32_t* ctr0, const uint32_t* key, uint64_t n, uint32_t* out)
+{
+    const rsos::RoundKeys rk = rsos::philox_round_keys(key[0], key[1]);
+    const uint64_t base = ((uint64_t)ctr0[1] << 32) | ctr0[0];
+    for (uint64_t b = 0; b < n; ++b) {
+        const uint64_t c01 = base + b;
+        const rsos::U4 r = rsos::philox4x32_10(rsos::U4{(uint32_t)c01, (uint32_t)(c01 >> 32), ctr0[2], ctr0[3]}, rk);
+        out[4 * b] = r.x; out[4 * b + 1] = r.y; out[4 * b + 2] = r.z; out[4 * b + 3] = r.w;
+    }
+}
+
 void probe_control(uint64_t seed, uint32_t t, int T, int order, int* out6)
 {
     const rsos::Control c = rsos::sweep_control((uint32_t)seed, (uint32_t)(seed >> 32), t, T, T, order);
