@@ -25,7 +25,7 @@ __all__ = [
     "rsos_last_cuda_error", "rsos_batch_create", "rsos_batch_schedule", "rsos_batch_run",
     "rsos_batch_poll", "rsos_batch_job", "rsos_batch_free", "rsos_set_moments", "rsos_moments",
     "rsos_read_moments", "rsos_autotune", "rsos_snapshot", "rsos_restore", "rsos_snapshot_bytes",
-    "library_path",
+    "rsos_peak_int", "rsos_checked_build", "rsos_bounds_errors", "library_path",
 ]
 
 RSOS_OK = 0
@@ -54,7 +54,9 @@ class RsosError(RuntimeError):
 
 
 class rsos_params(ctypes.Structure):
-    """Mirror of the C struct rsos_params (include/rsos.h)."""
+    """Mirror of the C struct rsos_params (include/rsos.h).  ``tile`` is a
+    square edge or a (Tx, Ty) pair; ``tiling=1`` selects the (+1) tilings of
+    section III.C, whose Tx, Ty are base edges."""
     _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("surfaces", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("phase_order", ctypes.c_int32),
                 ("series_capacity", ctypes.c_int32), ("engine", ctypes.c_int32), ("seed", ctypes.c_uint64),
