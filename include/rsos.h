@@ -11,7 +11,8 @@
  *     (multisurface coding, section II);
  *   - double tiling: Tx x Ty tiles, each split into 2 x 2 sub-tiles, four sets
  *     updated in turn, tiling origin moved randomly after every sweep
- *     (section II);
+ *     (section II); optionally the Tx(+1) x Ty(+1) tilings of the
+ *     decomposition check (section III.C);
  *   - time in sweeps; one sweep is L^2 expected attempts per surface (1 MCS);
  *   - observable: squared interface width W^2 = <h^2> - <h>^2 (Eq. 2), at
  *     measurement times such as those of Eq. 10.
@@ -52,7 +53,8 @@ typedef struct rsos_handle rsos_handle;
 typedef struct rsos_batch rsos_batch;
 
 /* Parameters of one job: S surfaces of one L x L lattice.
- *   L            periodic edge, L >= Tx, L % tile_x == 0 and L % tile_y == 0.
+ *   L            periodic edge, up to 65536; with tiling 0 a multiple of the
+ *                tile edge, with tiling 1 at least the base edges (see tiling).
  *   N            step bound of Eq. 6, 1 <= N <= 7 (coded in B = ceil(log2(2N+1))
  *                bits per site and surface).
  *   surfaces     S >= 1.  S == 1 runs the plain path (int32 heights, lane 0 of
