@@ -229,7 +229,9 @@ int rsos_launches(const rsos_handle* h, int64_t* out);
  *           offset 0;
  *   h00     the surfaces' absolute heights of site (0,0) (int64 each); in a
  *           caller-owned buffer at offset B*L*L*ceil(S/32)*4 rounded up to a
- *           multiple of 256, B = ceil(log2(2N+1));
+ *           multiple of 256, B = ceil(log2(2N+1)) (with tiling 1, L*L there
+ *           is L*T*ceil(L/T), T = tile_x: rows padded to whole column
+ *           classes);
  *   sums    device output, surfaces x 4 int64: sum h (low, high 64 bits) and
  *           sum h^2 (low, high) as two's-complement 128-bit integers.
  * Queued on stream, asynchronous; calls no cudaMalloc or cudaFree.  Scratch is
