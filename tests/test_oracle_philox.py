@@ -1,14 +1,67 @@
 """Pins for the oracle's Philox-4x32-10 (Salmon et al., SC'11).
 
-The Weyl constants have closed forms in that publication (golden ratio and
-sqrt(3)); the generator's output must look like independent fair bits.  The
-GPU suite additionally compares the oracle with cuRAND's device Philox.
+The generator's authors publish known-answer vectors with their reference
+implementation (tests/golden/philox4x32_10_kat.txt); they fix the
+multipliers, the Weyl constants, the round count and the order of the four
+output words.  The Weyl constants also have closed forms in that publication
+(golden ratio and sqrt(3)), and the output must look like independent fair
+bits.  The GPU suite additionally compares the oracle with cuRAND's device
+Philox.
 """
 import math
+import os
 
 import numpy as np
 
 import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+
+
+def read_kat(path=GOLDEN):
+    """(counter[4], key[2], expected[4]) per line of the known-answer file."""
+    out = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            words = [int(w, 16) for w in line]
+            assert len(words) == 10, line
+            out.append((words[0:4], words[4:6], words[6:10]))
+    return out
+
+
+def pi_words(n):
+    """First n 32-bit words of the fractional part of pi, from Machin's
+    formula pi = 16 atan(1/5) - 4 atan(1/239) in fixed-point integers."""
+    bits = 32 * n + 64  # guard bits
+    one = 1 << bits
+
+    def atan_inv(x):
+        total, term, k, x2 = 0, one // x, 1, x * x
+        while term:
+            total += term // k if (k // 2) % 2 == 0 else -(term // k)
+            term //= x2
+            k += 2
+        return total
+
+    pi = 16 * atan_inv(5) - 4 * atan_inv(239)
+    frac = (pi - 3 * one) >> 64
+    return [(frac >> (32 * (n - 1 - i))) & 0xFFFFFFFF for i in range(n)]
+
+
+def test_published_known_answer_vectors():
+    kat = read_kat()
+    assert len(kat) == 3
+    for ctr, key, expected in kat:
+        got = [int(v) for v in O.philox4x32_10(ctr, key)]
+        assert got == expected, ([hex(v) for v in got], [hex(v) for v in expected])
+
+
+def test_third_vector_inputs_are_the_digits_of_pi():
+    ctr, key, _ = read_kat()[2]
+    assert ctr + key == pi_words(6)
 
 
 def test_weyl_constants_closed_form():
