@@ -323,7 +323,7 @@ def cpu_baseline(L, N, T, seed, target_s: float = 12.0, tiling: int = 0):
             break
     value = float(L) * L * cores * done / el
     return {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} DT sweep(s) of L={L}, N={N}, {cores} lanes (one per thread) from the flat start"}
+            "sample": f"{done} DT sweep(s) of L={L}, N={N}, {cores} lanes, {cores} threads, from the flat start"}
 
 
 def run_batched(args):
@@ -478,7 +478,7 @@ def run_reference(args):
         O.sweeps(p, h, lanes, args.warmup + k, 1, threads=cores)
     el = time.perf_counter() - t0
     value = float(L) * L * cores * args.steps / el
-    sample = f"{args.steps} DT sweep(s) of L={L}, N={W['N']}, {cores} lanes (one per thread)"
+    sample = f"{args.steps} DT sweep(s) of L={L}, N={W['N']}, {cores} lanes, {cores} threads"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,

@@ -156,62 +156,118 @@ static int64_t* orc_at(int64_t* h, int32_t L, int32_t x, int32_t y)
 /* One attempt at (x, y): Eq. 6.  Returns 1 if the deposit was accepted. */
 static int orc_attempt(int64_t* h, int32_t L, int32_t N, int32_t x, int32_t y)
 {
-    int32_t xe = (x + 1) % L, xw = (x + L - 1) % L;
-    int32_t yn = (y + L - 1) % L, ys = (y + 1) % L;
+    /* periodic neighbours (0 <= x, y < L) */
+    int32_t xe = x + 1 == L ? 0 : x + 1, xw = x == 0 ? L - 1 : x - 1;
+    int32_t yn = y == 0 ? L - 1 : y - 1, ys = y + 1 == L ? 0 : y + 1;
     int64_t hx = *orc_at(h, L, x, y);
     int64_t nb[4] = {*orc_at(h, L, xe, y), *orc_at(h, L, xw, y),
                      *orc_at(h, L, x, yn), *orc_at(h, L, x, ys)};
+    int ok = 1;
     for (int m = 0; m < 4; ++m) {
         int64_t after = hx + 1 - nb[m];
-        if (after > N || after < -N) return 0;
+        ok &= (after <= N) & (after >= -N);
     }
-    *orc_at(h, L, x, y) = hx + 1;
-    return 1;
+    *orc_at(h, L, x, y) = hx + ok;
+    return ok;
 }
 
-/* One DT sweep (sweep index t) of a single lane.  Returns accepted deposits. */
-static int64_t orc_dt_sweep_lane(const orc_params* P, int64_t* h, uint32_t lane, uint64_t t)
+/* Lanes offered one selection together (lanes of one 32-lane word share
+ * their mask draws; eight keep the fields a thread touches few). */
+#define ORC_GROUP 8
+
+/*
+ * One activation of one sub-tile (section II): its 2a selections in order,
+ * each offered to every lane of the group.  The lanes of a job share the
+ * sequence of selected sites; lane j takes part in selection i only if bit
+ * (j & 31) of its mask word is set (the random half mask of the multisurface
+ * coding), and then makes one attempt of Eq. 6 on its own height field.
+ *   x0, y0    lattice coordinates of the sub-tile's first site (taken mod L)
+ *   sx, sy    extent of the sub-tile; a = sx sy
+ *   fields[m] height field of lane lanes[m], m < n <= ORC_GROUP
+ *   acc[m]    accepted deposits of lane m are added here
+ */
+static void orc_activate(const orc_params* P, int64_t* const* fields, const uint32_t* lanes, int n,
+                         uint32_t tile_id, uint64_t t, int p, int32_t x0, int32_t y0, int32_t sx, int32_t sy,
+                         int64_t* acc)
+{
+    const int32_t L = P->L;
+    const uint32_t a = (uint32_t)(sx * sy);
+    const uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    uint32_t site_r[4], mask_r[ORC_GROUP][4];
+    for (uint32_t i = 0; i < 2u * a; ++i) {
+        if ((i & 7u) == 0) {
+            uint32_t c[4] = {tile_id, (uint32_t)t, i >> 3, (2u << 30) | ((uint32_t)p << 28)};
+            orc_philox4x32_10(c, key, site_r);
+        }
+        if ((i & 3u) == 0) {
+            for (int m = 0; m < n; ++m) {
+                if (m > 0 && (lanes[m] >> 5) == (lanes[m - 1] >> 5)) {
+                    memcpy(mask_r[m], mask_r[m - 1], sizeof(mask_r[m]));  /* same word, same draw */
+                    continue;
+                }
+                uint32_t c[4] = {tile_id, (uint32_t)t, i >> 2,
+                                 (3u << 30) | ((uint32_t)p << 28) | (lanes[m] >> 5)};
+                orc_philox4x32_10(c, key, mask_r[m]);
+            }
+        }
+        uint32_t word = site_r[(i >> 1) & 3u];
+        uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
+        uint32_t k = (half * a) >> 16;
+        int32_t x = (x0 + (int32_t)(k % (uint32_t)sx)) % L;
+        int32_t y = (y0 + (int32_t)(k / (uint32_t)sx)) % L;
+        for (int m = 0; m < n; ++m) {
+            if ((mask_r[m][i & 3u] >> (lanes[m] & 31u)) & 1u) acc[m] += orc_attempt(fields[m], L, P->N, x, y);
+        }
+    }
+}
+
+/* The fields of lanes[g * ORC_GROUP ...] (at most ORC_GROUP of them). */
+static int orc_group(int64_t* h, int64_t area, int32_t n_lanes, int32_t g, int64_t** fields)
+{
+    int n = n_lanes - g * ORC_GROUP;
+    if (n > ORC_GROUP) n = ORC_GROUP;
+    for (int m = 0; m < n; ++m) fields[m] = h + (int64_t)(g * ORC_GROUP + m) * area;
+    return n;
+}
+
+/*
+ * One DT sweep (sweep index t) of n_lanes height fields (section II): the
+ * control draw fixes the tiling origin and the order of the four sub-tile
+ * sets; then, set after set, every tile activates its sub-tile of the set.
+ * The active sub-tiles of one set never touch each other's sites or halos,
+ * so the method updates them concurrently: here tile rows of a set run in
+ * parallel threads (each thread for one group of lanes), and the next set
+ * starts when all of them are done.  accepted[m] += deposits of field m.
+ */
+static void orc_dt_sweep(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n_lanes, uint64_t t,
+                         int32_t n_threads, int64_t* accepted)
 {
     const int32_t L = P->L, Tx = P->Tx, Ty = P->Ty;
     const int32_t sx = Tx / 2, sy = Ty / 2;
-    const uint32_t a = (uint32_t)(sx * sy);
     const int32_t ntx = L / Tx, nty = L / Ty;
-    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    const int64_t area = (int64_t)L * L;
+    const int32_t groups = (n_lanes + ORC_GROUP - 1) / ORC_GROUP;
     int32_t ox, oy, perm[4];
-    int64_t accepted = 0;
     orc_control(P, t, &ox, &oy, perm);
     for (int p = 0; p < 4; ++p) {
         const int q = perm[p];
         const int32_t qx = q & 1, qy = q >> 1;
-        for (int32_t ty = 0; ty < nty; ++ty) {
-            for (int32_t tx = 0; tx < ntx; ++tx) {
-                const uint32_t tile_id = (uint32_t)(ty * ntx + tx);
-                uint32_t site_r[4], mask_r[4];
-                for (uint32_t i = 0; i < 2u * a; ++i) {
-                    if ((i & 7u) == 0) {
-                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 3, (2u << 30) | ((uint32_t)p << 28)};
-                        orc_philox4x32_10(c, key, site_r);
-                    }
-                    if ((i & 3u) == 0) {
-                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 2,
-                                         (3u << 30) | ((uint32_t)p << 28) | (lane >> 5)};
-                        orc_philox4x32_10(c, key, mask_r);
-                    }
-                    uint32_t word = site_r[(i >> 1) & 3u];
-                    uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
-                    uint32_t k = (half * a) >> 16;
-                    uint32_t bit = (mask_r[i & 3u] >> (lane & 31u)) & 1u;
-                    if (!bit) continue;
-                    int32_t u = qx * sx + (int32_t)(k % (uint32_t)sx);
-                    int32_t v = qy * sy + (int32_t)(k / (uint32_t)sx);
-                    int32_t x = (ox + tx * Tx + u) % L;
-                    int32_t y = (oy + ty * Ty + v) % L;
-                    accepted += orc_attempt(h, L, P->N, x, y);
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) num_threads(n_threads)
+        for (int32_t g = 0; g < groups; ++g) {
+            for (int32_t ty = 0; ty < nty; ++ty) {
+                int64_t* fields[ORC_GROUP];
+                int64_t acc[ORC_GROUP] = {0};
+                const int n = orc_group(h, area, n_lanes, g, fields);
+                for (int32_t tx = 0; tx < ntx; ++tx)
+                    orc_activate(P, fields, lanes + g * ORC_GROUP, n, (uint32_t)(ty * ntx + tx), t, p,
+                                 ox + tx * Tx + qx * sx, oy + ty * Ty + qy * sy, sx, sy, acc);
+                for (int m = 0; m < n; ++m) {
+#pragma omp atomic
+                    accepted[g * ORC_GROUP + m] += acc[m];
                 }
             }
         }
     }
-    return accepted;
 }
 
 /*
@@ -245,51 +301,42 @@ void orc_axis_half(int32_t L, int32_t T, int32_t c, int32_t half, int32_t* start
     *width = half ? w - w0 : w0;
 }
 
-/* One DT sweep of a single lane on a (+1) tiling: as orc_dt_sweep_lane, with
+/* One DT sweep of n_lanes fields on a (+1) tiling: as orc_dt_sweep, with
  * the sub-tile of tile (tx, ty) in set q spanning the halves above, a its
  * area and 2a selections per activation. */
-static int64_t orc_dt_sweep_lane_general(const orc_params* P, int64_t* h, uint32_t lane, uint64_t t)
+static void orc_dt_sweep_general(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n_lanes,
+                                 uint64_t t, int32_t n_threads, int64_t* accepted)
 {
     const int32_t L = P->L;
     const orc_axis ax = orc_axis_of(L, P->Tx), ay = orc_axis_of(L, P->Ty);
-    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    const int64_t area = (int64_t)L * L;
+    const int32_t groups = (n_lanes + ORC_GROUP - 1) / ORC_GROUP;
     int32_t ox, oy, perm[4];
-    int64_t accepted = 0;
     orc_control(P, t, &ox, &oy, perm);
     for (int p = 0; p < 4; ++p) {
         const int q = perm[p];
         const int32_t qx = q & 1, qy = q >> 1;
-        for (int32_t ty = 0; ty < ay.n; ++ty) {
-            for (int32_t tx = 0; tx < ax.n; ++tx) {
-                const uint32_t tile_id = (uint32_t)(ty * ax.n + tx);
-                int32_t u0, sx, v0, sy;
-                orc_axis_half(L, P->Tx, tx, qx, &u0, &sx);
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) num_threads(n_threads)
+        for (int32_t g = 0; g < groups; ++g) {
+            for (int32_t ty = 0; ty < ay.n; ++ty) {
+                int64_t* fields[ORC_GROUP];
+                int64_t acc[ORC_GROUP] = {0};
+                const int n = orc_group(h, area, n_lanes, g, fields);
+                int32_t v0, sy;
                 orc_axis_half(L, P->Ty, ty, qy, &v0, &sy);
-                const uint32_t a = (uint32_t)(sx * sy);
-                uint32_t site_r[4], mask_r[4];
-                for (uint32_t i = 0; i < 2u * a; ++i) {
-                    if ((i & 7u) == 0) {
-                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 3, (2u << 30) | ((uint32_t)p << 28)};
-                        orc_philox4x32_10(c, key, site_r);
-                    }
-                    if ((i & 3u) == 0) {
-                        uint32_t c[4] = {tile_id, (uint32_t)t, i >> 2,
-                                         (3u << 30) | ((uint32_t)p << 28) | (lane >> 5)};
-                        orc_philox4x32_10(c, key, mask_r);
-                    }
-                    uint32_t word = site_r[(i >> 1) & 3u];
-                    uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
-                    uint32_t k = (half * a) >> 16;
-                    uint32_t bit = (mask_r[i & 3u] >> (lane & 31u)) & 1u;
-                    if (!bit) continue;
-                    int32_t x = (ox + u0 + (int32_t)(k % (uint32_t)sx)) % L;
-                    int32_t y = (oy + v0 + (int32_t)(k / (uint32_t)sx)) % L;
-                    accepted += orc_attempt(h, L, P->N, x, y);
+                for (int32_t tx = 0; tx < ax.n; ++tx) {
+                    int32_t u0, sx;
+                    orc_axis_half(L, P->Tx, tx, qx, &u0, &sx);
+                    orc_activate(P, fields, lanes + g * ORC_GROUP, n, (uint32_t)(ty * ax.n + tx), t, p, ox + u0,
+                                 oy + v0, sx, sy, acc);
+                }
+                for (int m = 0; m < n; ++m) {
+#pragma omp atomic
+                    accepted[g * ORC_GROUP + m] += acc[m];
                 }
             }
         }
     }
-    return accepted;
 }
 
 /* One random-sequential Monte-Carlo step (L^2 attempts) of a single lane. */
@@ -317,7 +364,8 @@ static int64_t orc_rs_step_lane(const orc_params* P, int64_t* h, uint32_t lane, 
  * is the lane index j of field m (it selects the mask bit and mask word).
  * rs != 0 selects the random-sequential dynamics instead of DT.
  * accepted (nullable) receives the accepted deposits per field.
- * Lanes are independent simulations; they run in parallel threads.
+ * DT: the tile rows of each sub-tile set run in parallel threads (orc_dt_sweep);
+ * RS: each lane is its own chain, one lane per thread.
  */
 int orc_sweeps(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n_lanes,
                uint64_t t0, uint64_t n_sweeps, int32_t rs, int32_t n_threads, int64_t* accepted)
@@ -334,16 +382,22 @@ int orc_sweeps(const orc_params* P, int64_t* h, const uint32_t* lanes, int32_t n
     }
     const int64_t area = (int64_t)P->L * P->L;
     if (n_threads < 1) n_threads = 1;
+    int64_t* acc = (int64_t*)calloc(n_lanes > 0 ? (size_t)n_lanes : 1u, sizeof(int64_t));
+    if (!acc) return -1;
+    if (rs) {
+        /* random-sequential steps: each lane is its own chain, one per thread */
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
-    for (int32_t m = 0; m < n_lanes; ++m) {
-        int64_t acc = 0;
-        for (uint64_t t = t0; t < t0 + n_sweeps; ++t) {
-            acc += rs ? orc_rs_step_lane(P, h + m * area, lanes[m], t)
-                      : P->tiling == 1 ? orc_dt_sweep_lane_general(P, h + m * area, lanes[m], t)
-                                       : orc_dt_sweep_lane(P, h + m * area, lanes[m], t);
+        for (int32_t m = 0; m < n_lanes; ++m) {
+            for (uint64_t t = t0; t < t0 + n_sweeps; ++t) acc[m] += orc_rs_step_lane(P, h + m * area, lanes[m], t);
         }
-        if (accepted) accepted[m] = acc;
+    } else {
+        for (uint64_t t = t0; t < t0 + n_sweeps; ++t) {
+            if (P->tiling == 1) orc_dt_sweep_general(P, h, lanes, n_lanes, t, n_threads, acc);
+            else orc_dt_sweep(P, h, lanes, n_lanes, t, n_threads, acc);
+        }
     }
+    if (accepted) memcpy(accepted, acc, (size_t)(n_lanes > 0 ? n_lanes : 0) * sizeof(int64_t));
+    free(acc);
     return 0;
 }
 
