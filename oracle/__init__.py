@@ -166,7 +166,11 @@ def sweeps(p: Params, h: np.ndarray, lanes, t0: int, n: int, rs: bool = False,
     assert ln.shape == (h.shape[0],)
     acc = np.zeros(h.shape[0], dtype=np.int64)
     if threads is None:
-        threads = max(1, min(os.cpu_count() or 1, h.shape[0]))
+        # DT sweeps run the tile rows of a sub-tile set in parallel; RS steps
+        # one lane per thread
+        threads = os.cpu_count() or 1
+        if rs:
+            threads = max(1, min(threads, h.shape[0]))
     pc = p.c()
     rc = lib.orc_sweeps(ctypes.byref(pc), _ptr(h, ctypes.c_int64), _ptr(ln, ctypes.c_uint32),
                         h.shape[0], t0, n, 1 if rs else 0, threads, _ptr(acc, ctypes.c_int64))

@@ -15,16 +15,21 @@ def _to128(lo, hi):
     return [(int(h) << 64) + (int(l) & 0xFFFFFFFFFFFFFFFF) for l, h in zip(lo, hi)]
 
 
-@pytest.mark.parametrize("L,N,S", [(256, 2, 64), (4096, 1, 64), (512, 4, 96)])
-def test_noalloc_width_equals_rsos_width_on_two_calls(L, N, S):
+@pytest.mark.parametrize("L,N,S,tiling,tile", [(256, 2, 64, 0, 8), (4096, 1, 64, 0, 8), (512, 4, 96, 0, 8),
+                                                (256, 1, 64, 1, (6, 10)), (100, 3, 32, 1, (7, 9))])
+def test_noalloc_width_equals_rsos_width_on_two_calls(L, N, S, tiling, tile):
     import torch
-    p = R.rsos_params(L=L, N=N, surfaces=S, tile=8, seed=123, series_capacity=4)
+    p = R.rsos_params(L=L, N=N, surfaces=S, tile=tile, seed=123, series_capacity=4, tiling=tiling)
     nbytes = R.rsos_required_bytes(p)
     buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
     base = (buf.data_ptr() + 255) // 256 * 256
     B = 2 if N <= 1 else (3 if N <= 3 else 4)
     NW = (S + 31) // 32
-    h00_off = (B * L * L * NW * 4 + 255) // 256 * 256
+    # site records per lattice: L * L, or with a (+1) tiling L rows of
+    # T * ceil(L / T) records (T = tile_x: rows padded to whole column classes)
+    T = tile[0] if isinstance(tile, tuple) else tile
+    records = L * T * ((L + T - 1) // T) if tiling else L * L
+    h00_off = (B * records * NW * 4 + 255) // 256 * 256
     out = torch.zeros(S * 4, dtype=torch.int64, device="cuda")
     h = R.rsos_init(p, dev_buf=base, dev_bytes=nbytes)
     try:
