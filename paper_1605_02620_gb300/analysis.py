@@ -23,19 +23,32 @@ from fractions import Fraction
 
 import numpy as np
 
+from .inputs import paper_schedule
 
-def schedule(t_max: int, m: float = 0.01, t0: float = 0.0) -> list:
-    """Measurement times of the paper (section II): t_{i+1} = (t_i + 10) e^m
-    from t_0 = 0, rounded up to whole sweeps, repeats dropped, up to t_max."""
-    out, t = [], float(t0)
-    while True:
-        T = int(np.ceil(t - 1e-9))
-        if T > t_max:
-            break
-        if not out or T > out[-1]:
-            out.append(T)
-        t = (t + 10.0) * np.exp(m)
-    return out
+
+def schedule(t_max: int, m: float = 0.01) -> list:
+    """Measurement times of the paper (Eq. 10, section II): the same list as
+    inputs.paper_schedule, t = 0 included."""
+    return paper_schedule(t_max, m=m)
+
+
+def jackknife(samples, estimator):
+    """Delete-one jackknife over the first axis of ``samples`` (one entry per
+    independent job): the estimate on the mean of all entries and its
+    standard error sqrt((n - 1) / n * sum_k (e_k - e_mean)^2), e_k the
+    estimate on the mean of all entries but k.  estimator maps a mean (one
+    entry's shape) to a number or an array."""
+    x = np.asarray(samples, dtype=np.float64)
+    n = x.shape[0]
+    if n < 2:
+        raise ValueError("the jackknife needs at least two samples")
+    full = np.asarray(estimator(x.mean(axis=0)), dtype=np.float64)
+    total = x.sum(axis=0)
+    reps = np.array([np.asarray(estimator((total - x[k]) / (n - 1)), dtype=np.float64) for k in range(n)])
+    err = np.sqrt((n - 1) / n * ((reps - reps.mean(axis=0)) ** 2).sum(axis=0))
+    if full.ndim == 0:
+        return float(full), float(err)
+    return full, err
 
 
 def standard_error(x) -> float:

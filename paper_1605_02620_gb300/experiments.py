@@ -1,16 +1,21 @@
 """Experiment drivers of section III on the library: growth runs (W^2 at the
-paper's measurement times and the effective growth exponent), steady-state
-widths and their finite-size scaling (the roughness exponent), and the
-decomposition check (the same scaling on several tilings, section III.C).
+paper's measurement times and the growth exponent), steady-state widths and
+their finite-size scaling (the roughness exponent), and the decomposition
+check (the same scaling on several tilings, section III.C).
 
 Host orchestration only: every sweep and every exact measurement runs in the
 library's kernels; this module chooses parameters and times and reduces the
-exact sums the library returns with ``analysis``.  Surfaces of one job share
-the selected sites (section II), so they are correlated samples; the paper
-averages over them as realizations, and the errors here do the same.
+exact sums the library returns with ``analysis``.
 
-    python -m paper_1605_02620_gb300.experiments growth --L 4096 --N 1 --t-max 10000
-    python -m paper_1605_02620_gb300.experiments fss --Ls 32 64 128 256 --surfaces 1024
+Errors.  The surfaces of one job share the selected sites (section II), so
+they are correlated samples of one Markov chain.  Every estimate here is
+therefore made from several independent jobs (different seeds; advanced
+together as one batch): each job contributes one sample (its mean over its
+surfaces), standard errors are the spread over jobs, and the errors of the
+exponents (local slopes and fits) are delete-one-job jackknife errors.
+
+    python -m paper_1605_02620_gb300.experiments growth --L 4096 --N 1 --t-max 10000 --jobs 8
+    python -m paper_1605_02620_gb300.experiments fss --Ls 32 64 128 256 512 --surfaces 64 --jobs 16
     python -m paper_1605_02620_gb300.experiments dd --Ls 64 128 --tilings 8x8 16x16 6x10+1
 """
 from __future__ import annotations
@@ -18,78 +23,132 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import time
 
 import numpy as np
 
 from . import analysis
-from . import rsos_free, rsos_init, rsos_params, rsos_read_series, rsos_schedule, rsos_sweep
+from . import (rsos_batch_create, rsos_batch_free, rsos_batch_job, rsos_batch_poll, rsos_batch_run,
+               rsos_batch_schedule, rsos_params, rsos_read_series)
 from .inputs import paper_schedule
 
 
-def _run(L, N, surfaces, times, seed, tile, tiling, stream=None):
-    """One job from the flat start, measured at ``times`` (ascending); returns
-    (times, w2[len(times)][surfaces]) from the exact sums."""
+def _run_jobs(L, N, surfaces, times, seeds, tile, tiling, stream=None):
+    """Independent jobs (one per seed) from the flat start, measured at
+    ``times`` (ascending), advanced together as one batch.  Returns
+    (times, w2[jobs][len(times)][surfaces]) from the exact sums."""
     times = [int(t) for t in times]
-    p = rsos_params(L=L, N=N, surfaces=surfaces, tile=tile, seed=seed, series_capacity=len(times) + 1,
-                    tiling=tiling)
-    h = rsos_init(p, stream=stream)
+    params = [rsos_params(L=L, N=N, surfaces=surfaces, tile=tile, seed=s, series_capacity=len(times) + 1,
+                          tiling=tiling) for s in seeds]
+    b = rsos_batch_create(params, [times[-1]] * len(params))
     try:
-        rsos_schedule(h, times)
-        rsos_sweep(h, times[-1], stream=stream)
-        ts, _, _, w2 = rsos_read_series(h, surfaces, len(times) + 1, stream=stream)
+        for k in range(len(params)):
+            rsos_batch_schedule(b, k, times)
+        rsos_batch_run(b, stream)
+        done = set()
+        while len(done) < len(params):
+            _, ids = rsos_batch_poll(b)
+            done |= set(ids)
+            if len(done) < len(params):
+                time.sleep(0.002)
+        w2 = []
+        for k in range(len(params)):
+            ts, _, _, w = rsos_read_series(rsos_batch_job(b, k), surfaces, len(times) + 1, stream)
+            if [int(t) for t in ts] != times:
+                raise RuntimeError(f"job {k} measured at {list(ts)}, expected {times}")
+            w2.append(np.asarray(w, dtype=np.float64))
     finally:
-        rsos_free(h)
-    return [int(t) for t in ts], np.asarray(w2, dtype=np.float64)
+        rsos_batch_free(b)
+    return times, np.stack(w2)
 
 
-def growth(L: int, N: int, t_max: int, surfaces: int = 64, seed: int = 0, tile=8, tiling: int = 0,
-           m: float = 0.01, stream=None) -> dict:
-    """Growth regime (Eq. 9): W^2 averaged over the surfaces at the paper's
-    measurement times (Eq. 10 with exponent m) up to t_max, its standard
-    error, and the effective exponent beta_eff from local slopes."""
+def _slope(x, y):
+    """Least-squares slope of y against x."""
+    return float(np.polyfit(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64), 1)[0])
+
+
+def growth(L: int, N: int, t_max: int, surfaces: int = 64, jobs: int = 8, seed: int = 0, tile=8, tiling: int = 0,
+           m: float = 0.01, window=None, stream=None) -> dict:
+    """Growth regime (Eq. 9): W^2 at the paper's measurement times (Eq. 10
+    with exponent m) up to t_max, averaged over the surfaces of `jobs`
+    independent jobs, with its standard error over jobs; the effective
+    exponent beta_eff from local slopes, with jackknife errors; and the growth
+    exponent fitted over a window of times: the slope of ln W against ln t
+    (beta_fit) and the two-correction form of Eq. 11 (beta_eq11), each with
+    its jackknife error.  window = (t_lo, t_hi), default the last decade."""
     times = [t for t in paper_schedule(t_max, m=m) if t > 0]
-    ts, w2 = _run(L, N, surfaces, times, seed, tile, tiling, stream)
-    mean = w2.mean(axis=1)
-    err = np.array([analysis.standard_error(row) for row in w2])
+    if len(times) < 2:
+        raise ValueError(f"t_max = {t_max} leaves fewer than two measurement times of Eq. 10 (m = {m})")
+    if jobs < 2:
+        raise ValueError("the errors need at least two independent jobs")
+    ts, w2 = _run_jobs(L, N, surfaces, times, [seed + k for k in range(jobs)], tile, tiling, stream)
+    per_job = w2.mean(axis=2)  # [jobs][times]
+    mean = per_job.mean(axis=0)
+    err = per_job.std(axis=0, ddof=1) / math.sqrt(jobs)
     t_mid, beff = analysis.beta_eff(ts, mean)
-    return {"L": L, "N": N, "surfaces": surfaces, "tile": tile, "tiling": tiling, "t": ts,
-            "w2": mean.tolist(), "w2_err": err.tolist(), "beta_eff_t": t_mid.tolist(),
-            "beta_eff": beff.tolist()}
+    beff_err = analysis.jackknife(per_job, lambda c: analysis.beta_eff(ts, c)[1])[1]
+    t_lo, t_hi = window if window else (t_max / 10.0, t_max)
+    sel = [i for i, t in enumerate(ts) if t_lo <= t <= t_hi]
+    if len(sel) < 3:
+        raise ValueError(f"the fit window {t_lo}..{t_hi} holds fewer than three measurement times")
+    lt = np.log(np.asarray(ts, dtype=np.float64)[sel])
+    fit = lambda c: 0.5 * _slope(lt, np.log(np.asarray(c)[sel]))  # noqa: E731
+    beta_fit, beta_fit_err = analysis.jackknife(per_job, fit)
+    # Eq. 11 on the local slopes from t >= 10 (the fit's own lower cut)
+    late = lambda c: [(tm, b) for tm, b in zip(*analysis.beta_eff(ts, c)) if tm >= 10.0]  # noqa: E731
+    eq11 = lambda c: analysis.fit_beta_two_power_laws(*zip(*late(c)))[0]  # noqa: E731
+    beta_eq11, beta_eq11_err = analysis.jackknife(per_job, eq11)
+    return {"L": L, "N": N, "surfaces": surfaces, "jobs": jobs, "tile": tile, "tiling": tiling, "t": ts,
+            "w2": mean.tolist(), "w2_err": err.tolist(), "beta_eff_t": t_mid.tolist(), "beta_eff": beff.tolist(),
+            "beta_eff_err": np.asarray(beff_err).tolist(), "window": [t_lo, t_hi], "beta_fit": beta_fit,
+            "beta_fit_err": beta_fit_err, "beta_eq11": beta_eq11, "beta_eq11_err": beta_eq11_err}
 
 
 def steady_width(L: int, N: int, t_start: int, n_samples: int = 40, every: int = 0, surfaces: int = 64,
-                 seed: int = 0, tile=8, tiling: int = 0, stream=None) -> dict:
+                 jobs: int = 8, seed: int = 0, tile=8, tiling: int = 0, stream=None) -> dict:
     """Steady state (Eq. 12): W^2 sampled every ``every`` sweeps (default
-    t_start / 40) from t_start on, averaged over samples and surfaces, with
-    the per-surface time averages as the samples of its error."""
+    t_start / 40) from t_start on, in `jobs` independent jobs.  Each job's
+    time and surface average is one sample: w2 is their mean, w2_err their
+    standard error; w2_jobs lists them."""
     every = every or max(1, t_start // 40)
     times = [t_start + k * every for k in range(n_samples)]
-    ts, w2 = _run(L, N, surfaces, times, seed, tile, tiling, stream)
-    per_surface = w2.mean(axis=0)
-    return {"L": L, "N": N, "t": ts, "w2": float(w2.mean()), "w2_err": analysis.standard_error(per_surface),
+    ts, w2 = _run_jobs(L, N, surfaces, times, [seed + k for k in range(jobs)], tile, tiling, stream)
+    per_job = w2.mean(axis=(1, 2))
+    return {"L": L, "N": N, "t": ts, "jobs": jobs, "w2": float(per_job.mean()),
+            "w2_err": analysis.standard_error(per_job), "w2_jobs": per_job.tolist(),
             "w2_samples": w2.reshape(-1).tolist()}
 
 
-def fss(Ls, N: int = 1, surfaces: int = 64, seed: int = 0, tile=8, tiling: int = 0, t_factor: float = 20.0,
-        z: float = 1.61, n_samples: int = 40, stream=None) -> dict:
-    """Finite-size scaling of the saturated width (Eq. 12): for every L a
-    steady-state run started at t_factor * L^z sweeps (past t_steady ~ L^z,
-    z = alpha / beta), then the local slopes alpha_eff between L and L/2, the
-    least-squares slope of ln W against ln L, and the skewness and kurtosis
-    of P(W^2) per L (section III.C)."""
+def fss(Ls, N: int = 1, surfaces: int = 64, jobs: int = 8, seed: int = 0, tile=8, tiling: int = 0,
+        t_factor: float = 20.0, z: float = 1.61, n_samples: int = 40, stream=None) -> dict:
+    """Finite-size scaling of the saturated width (Eq. 12): for every L,
+    `jobs` independent steady-state runs started at t_factor * L^z sweeps
+    (past t_steady ~ L^z, z = alpha / beta); then the local slopes alpha_eff
+    between L and L/2 and the least-squares slope alpha_fit of ln W against
+    ln L, each with its jackknife error over jobs, and the skewness and
+    kurtosis of P(W^2) per L (section III.C)."""
     Ls = sorted(int(L) for L in Ls)
+    if jobs < 2:
+        raise ValueError("the errors need at least two independent jobs")
     rows = []
     for L in Ls:
         r = steady_width(L, N, int(math.ceil(t_factor * L ** z)), n_samples=n_samples, surfaces=surfaces,
-                         seed=seed + L, tile=tile, tiling=tiling, stream=stream)
+                         jobs=jobs, seed=seed + 1000 * L, tile=tile, tiling=tiling, stream=stream)
         S, Q = analysis.distribution_shape(r.pop("w2_samples"))
         r.update(S=S, Q=Q)
         rows.append(r)
-    w2 = [r["w2"] for r in rows]
+    per_job = np.array([r["w2_jobs"] for r in rows]).T  # [jobs][Ls]: job k of every L is one jackknife unit
+    w2 = per_job.mean(axis=0)
     L_mid, a_eff = analysis.alpha_eff(Ls, w2)
-    slope = float(np.polyfit(np.log(Ls), 0.5 * np.log(w2), 1)[0]) if len(Ls) >= 2 else float("nan")
-    return {"N": N, "surfaces": surfaces, "tile": tile, "tiling": tiling, "rows": rows,
-            "alpha_eff_L": L_mid.tolist(), "alpha_eff": a_eff.tolist(), "alpha_fit": slope}
+    a_err = analysis.jackknife(per_job, lambda c: analysis.alpha_eff(Ls, c)[1])[1]
+    lL = np.log(np.asarray(Ls, dtype=np.float64))
+    if len(Ls) >= 2:
+        alpha_fit, alpha_err = analysis.jackknife(per_job, lambda c: 0.5 * _slope(lL, np.log(c)))
+    else:
+        alpha_fit, alpha_err = float("nan"), float("nan")
+    return {"N": N, "surfaces": surfaces, "jobs": jobs, "tile": tile, "tiling": tiling, "rows": rows,
+            "alpha_eff_L": L_mid.tolist(), "alpha_eff": a_eff.tolist(), "alpha_eff_err": np.asarray(a_err).tolist(),
+            "alpha_fit": alpha_fit, "alpha_fit_err": alpha_err}
 
 
 def dd_consistency(Ls, tilings, **kw) -> dict:
@@ -124,6 +183,7 @@ def main(argv=None):
     for sp in (g, sub.add_parser("fss"), sub.add_parser("dd")):
         sp.add_argument("--N", type=int, default=1)
         sp.add_argument("--surfaces", type=int, default=64)
+        sp.add_argument("--jobs", type=int, default=8)
         sp.add_argument("--seed", type=int, default=0)
         if sp is not g:
             sp.add_argument("--Ls", type=int, nargs="+", default=[32, 64, 128, 256])
@@ -134,12 +194,13 @@ def main(argv=None):
     a = ap.parse_args(argv)
     tile, tiling = parse_tiling(a.tiling)
     if a.cmd == "growth":
-        res = growth(a.L, a.N, a.t_max, surfaces=a.surfaces, seed=a.seed, tile=tile, tiling=tiling)
+        res = growth(a.L, a.N, a.t_max, surfaces=a.surfaces, jobs=a.jobs, seed=a.seed, tile=tile, tiling=tiling)
     elif a.cmd == "fss":
-        res = fss(a.Ls, a.N, surfaces=a.surfaces, seed=a.seed, tile=tile, tiling=tiling, t_factor=a.t_factor)
+        res = fss(a.Ls, a.N, surfaces=a.surfaces, jobs=a.jobs, seed=a.seed, tile=tile, tiling=tiling,
+                  t_factor=a.t_factor)
     else:
-        res = dd_consistency(a.Ls, [parse_tiling(s) for s in a.tilings], N=a.N, surfaces=a.surfaces, seed=a.seed,
-                             t_factor=a.t_factor)
+        res = dd_consistency(a.Ls, [parse_tiling(s) for s in a.tilings], N=a.N, surfaces=a.surfaces, jobs=a.jobs,
+                             seed=a.seed, t_factor=a.t_factor)
     print(json.dumps(res))
 
 

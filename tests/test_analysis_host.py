@@ -21,6 +21,43 @@ def test_schedule_follows_the_recursion():
     assert abs(n - 100 * math.log(1010 / 20)) < 3
 
 
+def test_schedule_is_the_inputs_schedule():
+    from paper_1605_02620_gb300.inputs import paper_schedule
+    for t_max in (0, 5, 11, 1000, 123457):
+        for m in (0.01, 0.05):
+            assert A.schedule(t_max, m=m) == paper_schedule(t_max, m=m)
+
+
+def test_jackknife_of_the_mean_is_the_standard_error():
+    # for the mean (a linear estimator) the delete-one jackknife error equals
+    # the standard error s / sqrt(n) exactly, entry by entry
+    rng = np.random.Generator(np.random.PCG64(11))
+    x = rng.normal(3.0, 2.0, size=(9, 5))
+    est, err = A.jackknife(x, lambda c: c)
+    assert np.allclose(est, x.mean(axis=0))
+    assert np.allclose(err, x.std(axis=0, ddof=1) / math.sqrt(9), rtol=1e-12)
+    # a scalar linear functional: the same identity
+    w = np.array([1.0, -2.0, 0.5, 3.0, 1.0])
+    e, s = A.jackknife(x, lambda c: float(w @ c))
+    assert e == pytest.approx(float(w @ x.mean(axis=0))) and s == pytest.approx((x @ w).std(ddof=1) / 3.0)
+    with pytest.raises(ValueError):
+        A.jackknife(x[:1], lambda c: c)
+
+
+def test_jackknife_of_a_log_slope_matches_the_delta_method():
+    # slope of ln y against ln x from noisy power laws: the jackknife error of
+    # the slope agrees with the propagated error of independent samples
+    rng = np.random.Generator(np.random.PCG64(12))
+    xs = np.array([32.0, 64.0, 128.0, 256.0])
+    n, rel = 400, 0.01
+    samples = 0.9 * xs ** 0.78 * (1 + rel * rng.standard_normal((n, len(xs))))
+    slope = lambda c: float(np.polyfit(np.log(xs), np.log(c), 1)[0])  # noqa: E731
+    est, err = A.jackknife(samples, slope)
+    lx = np.log(xs) - np.log(xs).mean()
+    delta = rel / math.sqrt(n) * math.sqrt(float((lx ** 2).sum())) / float((lx ** 2).sum())
+    assert est == pytest.approx(0.78, abs=5 * delta) and err == pytest.approx(delta, rel=0.15)
+
+
 def test_beta_eff_of_a_power_law_is_exact():
     t = np.array(A.schedule(20000)[1:], dtype=float)
     for beta in (0.2415, 0.25, 1 / 3):

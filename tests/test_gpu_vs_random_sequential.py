@@ -1,9 +1,12 @@
 """The GPU's double-tiling (DT) dynamics against a true random-sequential (RS)
 oracle (one uniformly random site per attempt, no domains).  The domain
-decomposition lowers the width's amplitude by a few per cent (the N -> inf
-closed forms already differ by the factor 1 - 1/(2a)), so the comparison is
-on what the paper's use of DT rests on: the same growth exponent, curves
-W_DT(t) / W_RS(t) parallel in time, and the same roughness exponent."""
+decomposition lowers the width's amplitude by a few per cent: the exact
+chains of tiny lattices put the DT stationary width below the RS one, and the
+N -> inf closed forms differ by the factor 1 - 1/(2a).  So the comparison is
+on what the paper's use of DT rests on: the same growth exponent, an
+amplitude ratio W_DT^2(t) / W_RS^2(t) that is constant in time within its
+errors (and below 1, the sign the exact chains fix), and the same roughness
+exponent."""
 import math
 import os
 
@@ -49,12 +52,19 @@ def test_growth_exponent_and_parallel_curves():
     se = math.sqrt(bd.var(ddof=1) / len(bd) + br.var(ddof=1) / len(br))
     assert abs(bd.mean() - br.mean()) < 3 * se, (bd.mean(), br.mean(), se)
     assert 0.20 < bd.mean() < 0.28 and 0.20 < br.mean() < 0.28
-    # amplitude ratio: a few per cent, the same early and late
-    ratio = dt.mean(axis=0) / rs.mean(axis=0)
-    rel = lambda b: b.std(axis=0, ddof=1) / math.sqrt(len(b)) / b.mean(axis=0)
-    dr = ratio * np.sqrt(rel(dt) ** 2 + rel(rs) ** 2)
-    assert np.all(np.abs(ratio - 1) < 0.12), ratio
-    assert abs(ratio[1] - ratio[-2]) < 3 * math.hypot(dr[1], dr[-2]), (ratio, dr)
+    # amplitude ratio of W^2 at every time from t = 32 on (t = 16 is two
+    # tile widths of growth), with its error from the block spreads; the
+    # weighted mean over times, and every time within 3 sigma of it (the
+    # curves are parallel: no exponent difference)
+    ratio = (dt.mean(axis=0) / rs.mean(axis=0))[1:]
+    rel = lambda b: b.std(axis=0, ddof=1) / math.sqrt(len(b)) / b.mean(axis=0)  # noqa: E731
+    dr = ratio * np.sqrt(rel(dt) ** 2 + rel(rs) ** 2)[1:]
+    wgt = 1.0 / dr ** 2
+    mean = float((ratio * wgt).sum() / wgt.sum())
+    err = float(1.0 / math.sqrt(wgt.sum()))
+    print(f"W2_DT / W2_RS at L = {L}: {mean:.4f} +- {err:.4f}; per time {np.round(ratio, 4).tolist()}")
+    assert np.all(np.abs(ratio - mean) < 3 * dr), (ratio, dr, mean)
+    assert mean < 1.0 - 3 * err, (mean, err)
 
 
 def test_roughness_exponent_matches_rs():
