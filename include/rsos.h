@@ -70,8 +70,10 @@ typedef struct rsos_batch rsos_batch;
  *                1: fixed order 0,1,2,3.
  *   series_capacity  number of measurements the device series buffer holds
  *                (0 means 1024).
- *   engine       0 auto, 1 one launch per phase, 2 persistent dataflow kernel.
- *                Every engine gives bit-identical results.
+ *   engine       0 auto (the persistent engine for multisurface jobs on a
+ *                regular tiling with at least 8 tile rows), 1 one launch per
+ *                phase, 2 persistent dataflow kernel.  Every engine gives
+ *                bit-identical results.
  *   seed         Philox key of the job.
  * Execution geometry of the persistent engine (no counterpart in the paper;
  * results are bit-identical for every choice; 0 = automatic, see
@@ -88,9 +90,12 @@ typedef struct rsos_batch rsos_batch;
  *                into floor(w/2) and the rest, and the per-sweep origin is
  *                uniform over one period of the pattern (T if T divides L,
  *                else L).  With T even and dividing L it is the regular
- *                tiling, bit for bit.  Multisurface jobs (surfaces >= 2) on
- *                the one-launch-per-phase engine (engine 0 or 1) only; the
- *                lattice rows hold T ceil(L / T) site records (T = tile_x). */
+ *                tiling, bit for bit.  Multisurface jobs (surfaces >= 2)
+ *                only; engine 0 (auto) and 1 run one launch per phase,
+ *                engine 2 the persistent engine, whose windows (the widest
+ *                half of either axis plus halo) must fit a block (RSOS_EINVAL
+ *                otherwise); the lattice rows hold T ceil(L / T) site records
+ *                (T = tile_x). */
 typedef struct {
     int32_t L;
     int32_t N;
@@ -128,11 +133,16 @@ int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_params* tuned,
                   void* stream);
 
 /* Create a job at time t = 0 with the flat initial condition (section II).
- *   dev_buf/dev_bytes  NULL/0: the library allocates and later frees the device
- *                memory; otherwise a caller-owned device buffer of at least
- *                rsos_required_bytes bytes, 256-byte aligned, that must outlive
- *                the handle (the library never frees it).
- *   stream       initialisation kernels are queued on it (asynchronous).
+ *   dev_buf/dev_bytes  NULL/0: the library allocates the device memory from
+ *                its stream-ordered pool on `stream` (no device-wide
+ *                synchronisation; blocks released by rsos_free are reused)
+ *                and later frees it; otherwise a caller-owned device buffer
+ *                of at least rsos_required_bytes bytes, 256-byte aligned, that
+ *                must outlive the handle (the library never frees it).
+ *   stream       the allocation and the initialisation kernels are queued on
+ *                it (asynchronous).  Later calls may use other streams: a
+ *                call on a stream other than that of the handle's previous
+ *                call first makes its stream wait for the earlier work.
  *   out          receives the handle (set to NULL on error).                  */
 int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* stream,
               rsos_handle** out);
@@ -239,8 +249,10 @@ int rsos_launches(const rsos_handle* h, int64_t* out);
  * loading the library keeps until the process exits; lattices whose
  * measurement needs more (about 4*L*32*ceil(S/32) bytes plus per-column sums)
  * get RSOS_ERANGE.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process,
+ * so make that first call before any stream capture, and do not call it
+ * again on a device after cudaDeviceReset (the array may then live at another
+ * address).  Every call reuses the same array: calls that overlap on the GPU
  * (different streams or host threads) race and must be serialised by the
  * caller.  RSOS_EINVAL for invalid params, NULL pointers or a single-surface
  * job, RSOS_ECUDA if a CUDA call fails. */
@@ -252,7 +264,10 @@ int rsos_width_noalloc(const rsos_params* params, const uint32_t* planes, const 
 int rsos_time(const rsos_handle* h, int64_t* t_out);
 
 /* Release the handle and the device memory it allocated.  NULL-safe.
- * Synchronises the device before freeing. */
+ * Stream-ordered: the memory goes back to the library's device memory pool
+ * once the work last queued through the handle (on the stream of its most
+ * recent call, which must still exist) has finished; neither the host nor
+ * the device waits. */
 int rsos_free(rsos_handle* h);
 
 /* Static description of a status code. */

@@ -47,12 +47,18 @@ struct rsos_handle {
     size_t smem_budget;
     // persistent engine
     bool persist;
+    int rows;  // tile rows of its items (L / T; L div Ty on a (+1) tiling)
     rsos::PersistPlan plan;
     unsigned long long* done;
     unsigned long long* ticket;
     unsigned int* err;
     long long budget_ns;
     int64_t launches;  // kernels queued by this handle
+    // Stream of the handle's most recent work; a call on another stream first
+    // waits for it (an event recorded on the old stream), so work queued
+    // through the handle stays in order whatever streams the caller uses.
+    cudaStream_t last_stream;
+    cudaEvent_t switch_ev;
 };
 
 namespace {
@@ -71,6 +77,7 @@ struct Layout {
     int ncb, S_pad, B, NW, T, cap;
     int nTc;    // class columns per row of the layout
     int CW, K;  // persistent engine: tiles per block, chunks per tile row
+    int rows;   // persistent engine: tile rows (L / Ty)
     bool plain, persist_on;
 };
 
@@ -116,6 +123,19 @@ int words_per_thread(const rsos_params* p, int NW)
     return 2;
 }
 
+// Windows of the (+1)-tiling persistent engine (the widest half of either
+// axis plus its halo, per thread of a block of kGenPersistWarps warps) fit a
+// block's shared memory.
+bool gen_persist_fits(const rsos_params* p)
+{
+    const int T = p->tile_x == 0 ? 8 : p->tile_x, Ty = p->tile_y == 0 ? 8 : p->tile_y;
+    const rsos::GenTiling G = rsos::gen_tiling(p->L, T, Ty);
+    const int NW = (p->surfaces + 31) / 32;
+    const size_t per_thread =
+        (size_t)(G.max_w + 2) * (G.max_h + 2) * rsos::bits_for_step(p->N) * 4 * (size_t)words_per_thread(p, NW);
+    return per_thread * 32 * rsos::kGenPersistWarps <= 227 * 1024;
+}
+
 int validate(const rsos_params* p)
 {
     if (!p) return RSOS_EINVAL;
@@ -127,7 +147,7 @@ int validate(const rsos_params* p)
         // of 32 threads within one block's shared memory.
         if (T > 30 || Ty > 30 || p->L > 65536) return RSOS_EINVAL;
         if (!rsos::gen_axis_valid(p->L, T) || !rsos::gen_axis_valid(p->L, Ty)) return RSOS_EINVAL;
-        if (p->surfaces < 2 || p->engine == 2) return RSOS_EINVAL;
+        if (p->surfaces < 2) return RSOS_EINVAL;
         if (p->N < 1 || p->N > 7 || p->surfaces > (1 << 20)) return RSOS_EINVAL;
         if (p->words_per_thread < 0 || p->words_per_thread > 2) return RSOS_EINVAL;
         const rsos::GenTiling G = rsos::gen_tiling(p->L, T, Ty);
@@ -135,6 +155,7 @@ int validate(const rsos_params* p)
         const size_t per_thread = (size_t)(G.max_w + 2) * (G.max_h + 2) * rsos::bits_for_step(p->N) * 4 *
                                   (size_t)words_per_thread(p, NWc);
         if (per_thread * 32 > 200 * 1024) return RSOS_EINVAL;
+        if (p->engine == 2 && !gen_persist_fits(p)) return RSOS_EINVAL;
     } else {
         if (p->tiling != 0) return RSOS_EINVAL;
         if (T != Ty) return RSOS_EINVAL;
@@ -190,10 +211,17 @@ Layout layout_of(const rsos_params* p)
     l.row0 = l.plain ? 0 : align256((size_t)l.S_pad * L * 4);
     l.partial = align256((size_t)l.ncb * l.S_pad * 6 * 8);  // moments need 6 words per entry
     l.rec = align256((size_t)(l.cap + 1) * l.S_pad * kRecWords * 8);
-    const int nT = p->L / l.T;
-    // Auto engine: the persistent dataflow engine for multisurface jobs with
-    // at least 8 tile rows, one launch per phase otherwise.
-    l.persist_on = !l.plain && p->tiling == 0 && (p->engine == 2 || (p->engine == 0 && nT >= 8));
+    // tiles per row and tile rows (a (+1) tiling: L div T of each axis)
+    const int Ty = p->tile_y == 0 ? 8 : p->tile_y;
+    const int nT = p->L / l.T;  // tiles per row (L div Tx on a (+1) tiling)
+    l.rows = p->tiling == 1 ? p->L / Ty : nT;
+    // Auto engine: the persistent dataflow engine for regular multisurface
+    // jobs with at least 8 tile rows, one launch per phase otherwise.  On a
+    // (+1) tiling the persistent engine runs only when asked for (engine 2):
+    // its windows, sized for the widest half, leave 9 warps per SM (6(+1) x
+    // 10(+1)), and at L = 9605 it measured 1.37 ms per sweep against the
+    // phase engine's 1.29.
+    l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && p->tiling == 0 && l.rows >= 8));
     if (l.persist_on && p->engine == 0) {
         // more lane-word groups than lanes of a warp: phase engine
         const int NWT = words_per_thread(p, l.NW);
@@ -205,7 +233,7 @@ Layout layout_of(const rsos_params* p)
         const int NWT = words_per_thread(p, l.NW);
         l.CW = persist_block_tiles(p, l.NW / NWT);
         l.K = (nT + l.CW - 1) / l.CW;
-        l.persist = align256((size_t)4 * nT * 8) + 256;
+        l.persist = align256((size_t)4 * l.rows * 8) + 256;
     }
     l.check = 256;  // checked build: out-of-range access counter (last region)
     l.total = l.planes + l.h00 + l.row0 + l.partial + l.rec + l.persist + l.check;
@@ -221,6 +249,69 @@ int fail_cuda(rsos_handle* h, cudaError_t e)
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Stream of a call on handle h: when it differs from the stream of the
+// handle's previous work, the new stream waits for that work first.
+cudaStream_t use_stream(rsos_handle* h, void* stream)
+{
+    const cudaStream_t s = as_stream(stream);
+    if (s != h->last_stream) {
+        if (cudaEventRecord(h->switch_ev, h->last_stream) == cudaSuccess) cudaStreamWaitEvent(s, h->switch_ev, 0);
+        h->last_stream = s;
+    }
+    return s;
+}
+
+// Library-owned device memory comes from one stream-ordered pool per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync): creating and releasing a job
+// never synchronises the device, so a serving loop can admit and retire jobs
+// while others run.  Released blocks stay cached in the pool (up to a quarter
+// of the device memory) for the next jobs.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t* out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            uint64_t keep = total_b / 4;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// bytes of device memory, ordered on stream s, 256-byte aligned.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e == cudaSuccess && (reinterpret_cast<uintptr_t>(*p) & 255u)) {
+        cudaFreeAsync(*p, s);
+        *p = nullptr;
+        e = cudaErrorMisalignedAddress;
+    }
+    return e;
+}
 
 // Exact 128-bit (lo, hi) pair -> int64 with overflow flag.
 bool fits64(int64_t lo, int64_t hi) { return hi == (lo < 0 ? -1 : 0); }
@@ -328,16 +419,49 @@ rsos::PersistArgs persist_args(const rsos_handle* h, uint32_t t0, int64_t n)
     return A;
 }
 
+// The (+1)-tiling engine's arguments: the same fields over the tiling's rows.
+rsos::GenPersistArgs gen_persist_args(const rsos_handle* h, uint32_t t0, int64_t n)
+{
+    const rsos::PersistArgs R = persist_args(h, t0, n);
+    rsos::GenPersistArgs A;
+    A.J = R.J;
+    A.G = h->G;
+    A.S.L = h->J.L;
+    A.S.y = h->G.y;
+    A.S.Px = rsos::gen_period(h->J.L, h->p.tile_x);
+    A.S.Py = rsos::gen_period(h->J.L, h->p.tile_y);
+    A.S.K = h->plan.K;
+    A.S.D = h->plan.D;
+    A.S.phase_order = h->p.phase_order;
+    A.S.seed_lo = h->J.seed_lo;
+    A.S.seed_hi = h->J.seed_hi;
+    A.done = R.done;
+    A.ticket = R.ticket;
+    A.err = R.err;
+    A.t0 = t0;
+    A.n_tickets = (unsigned long long)n * 4ull * (unsigned long long)h->rows * (unsigned long long)h->plan.K;
+    A.CW = R.CW;
+    A.TPL = R.TPL;
+    A.budget_ns = R.budget_ns;
+    return A;
+}
+
+// One persistent launch of sweeps [t0, t0 + n) (after the ticket reset).
+cudaError_t launch_job_persist(rsos_handle* h, uint32_t t0, int64_t n, cudaStream_t s)
+{
+    return h->general ? rsos::launch_gen_persist(h->p.N, h->NWT, gen_persist_args(h, t0, n), h->plan, s)
+                      : rsos::launch_persist(h->J, h->SX, h->NWT, persist_args(h, t0, n), h->plan, s);
+}
+
 int run_persist_segment(rsos_handle* h, int64_t n, cudaStream_t s)
 {
     // Tickets of one launch stay below 2^31: split very long segments.
-    const int64_t per_sweep = 4ll * h->J.nT * h->plan.K;
+    const int64_t per_sweep = 4ll * h->rows * h->plan.K;
     const int64_t max_sweeps = std::max<int64_t>(1, ((int64_t)1 << 31) / per_sweep);
     while (n > 0) {
         const int64_t m = std::min(n, max_sweeps);
         cudaError_t e = rsos::launch_zero(h->ticket, 8, s);
-        if (e == cudaSuccess)
-            e = rsos::launch_persist(h->J, h->SX, h->NWT, persist_args(h, (uint32_t)h->t, m), h->plan, s);
+        if (e == cudaSuccess) e = launch_job_persist(h, (uint32_t)h->t, m, s);
         if (e != cudaSuccess) return fail_cuda(h, e);
         h->launches += 2;
         h->t += m;
@@ -505,13 +629,20 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
         if (v >= 4096 && v <= 232448) h->smem_budget = (size_t)v;
     }
     h->bytes = l.total;
+    h->last_stream = as_stream(stream);
+    if (cudaEventCreateWithFlags(&h->switch_ev, cudaEventDisableTiming) != cudaSuccess) {
+        g_init_cuda_err = (int)cudaGetLastError();
+        delete h;
+        return RSOS_ECUDA;
+    }
     if (dev_buf) {
         h->base = static_cast<unsigned char*>(dev_buf);
         h->owns = false;
     } else {
         void* p = nullptr;
-        const cudaError_t e = cudaMalloc(&p, l.total);
+        const cudaError_t e = pool_alloc(&p, l.total, h->last_stream);
         if (e != cudaSuccess) {
+            cudaEventDestroy(h->switch_ev);
             delete h;
             (void)cudaGetLastError();
             return RSOS_ENOMEM;
@@ -538,10 +669,10 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     h->ticket = nullptr;
     h->err = nullptr;
     h->budget_ns = 1000000000ll;
+    h->rows = l.rows;
     if (l.persist_on) {
-        const int nT = params->L / l.T;
         h->done = reinterpret_cast<unsigned long long*>(cur);
-        cur += align256((size_t)4 * nT * 8);
+        cur += align256((size_t)4 * l.rows * 8);
         h->ticket = reinterpret_cast<unsigned long long*>(cur);
         h->err = reinterpret_cast<unsigned int*>(cur + 8);
     }
@@ -559,9 +690,10 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     J.bounds_err = reinterpret_cast<uint32_t*>(h->base + (l.total - l.check));
     cudaError_t e = cudaSuccess;
     if (l.persist_on) {
-        e = rsos::plan_persist(J, h->SX, h->NWT, l.CW, params->phase_lag, &h->plan);
+        e = h->general ? rsos::plan_gen_persist(J, h->G, h->NWT, l.CW, params->phase_lag, &h->plan)
+                       : rsos::plan_persist(J, h->SX, h->NWT, l.CW, params->phase_lag, &h->plan);
         if (e == cudaSuccess && (h->plan.CW != l.CW || h->plan.K != l.K)) e = cudaErrorInvalidConfiguration;
-        if (e == cudaSuccess) e = rsos::launch_zero(h->done, (size_t)4 * J.nT * 8, as_stream(stream));
+        if (e == cudaSuccess) e = rsos::launch_zero(h->done, (size_t)4 * l.rows * 8, as_stream(stream));
         if (e == cudaSuccess) e = rsos::launch_zero(h->ticket, 16, as_stream(stream));
     }
     // Flat initial condition (section II): planes and h00 zero.
@@ -570,7 +702,8 @@ int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* 
     if (e != cudaSuccess) {
         g_init_cuda_err = (int)e;
         (void)cudaGetLastError();
-        if (h->owns) cudaFree(h->base);
+        if (h->owns) cudaFreeAsync(h->base, h->last_stream);
+        cudaEventDestroy(h->switch_ev);
         delete h;
         return RSOS_ECUDA;
     }
@@ -587,7 +720,7 @@ int rsos_sweep(rsos_handle* h, int64_t n_sweeps, void* stream)
     size_t due = 0;
     for (size_t k = h->sched_pos; k < h->sched.size() && h->sched[k] <= h->t + n_sweeps; ++k) ++due;
     if (h->series_t.size() + due > (size_t)h->cap) return RSOS_ERANGE;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     int rc = measure_due(h, s);
     if (rc) return rc;
     const int64_t t_end = h->t + n_sweeps;
@@ -619,7 +752,7 @@ int rsos_checked_build(void)
 int rsos_bounds_errors(rsos_handle* h, uint32_t* count, void* stream)
 {
     if (!h || !count) return RSOS_EINVAL;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     cudaError_t e = cudaMemcpyAsync(count, h->J.bounds_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return fail_cuda(h, e);
@@ -630,15 +763,14 @@ int rsos_selftest_timeout(rsos_handle* h, int64_t budget_ns, void* stream)
     if (!h || budget_ns <= 0) return RSOS_EINVAL;
     if (!h->persist) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     // Sweep t + 2 depends on sweep t + 1, which never runs: every wait of
     // this launch expires after budget_ns.
     const long long saved = h->budget_ns;
     h->budget_ns = budget_ns;
-    rsos::PersistArgs A = persist_args(h, (uint32_t)(h->t + 2), 1);
-    h->budget_ns = saved;
     cudaError_t e = rsos::launch_zero(h->ticket, 8, s);
-    if (e == cudaSuccess) e = rsos::launch_persist(h->J, h->SX, h->NWT, A, h->plan, s);
+    if (e == cudaSuccess) e = launch_job_persist(h, (uint32_t)(h->t + 2), 1, s);
+    h->budget_ns = saved;
     if (e != cudaSuccess) return fail_cuda(h, e);
     unsigned int v = 0;
     e = cudaMemcpyAsync(&v, h->err, sizeof(v), cudaMemcpyDeviceToHost, s);
@@ -655,7 +787,7 @@ int rsos_width(rsos_handle* h, int64_t* sum_h, int64_t* sum_h2, double* w2, int6
 {
     if (!h || !sum_h || !sum_h2) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     int rc = check_device_error(h, s);
     if (rc) return rc;
     rc = measure_into(h, h->cap, s, false);
@@ -687,7 +819,7 @@ int rsos_read_series(rsos_handle* h, int64_t* times, int64_t* sum_h, int64_t* su
 {
     if (!h || cap < 0 || !n_out) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     const int rc = check_device_error(h, s);
     if (rc) return rc;
     const int n = std::min<int>(cap, (int)h->series_t.size());
@@ -718,7 +850,7 @@ int rsos_moments(rsos_handle* h, int64_t* sums, int64_t* t_out, void* stream)
 {
     if (!h || !sums) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     int rc = check_device_error(h, s);
     if (rc) return rc;
     rc = measure_into(h, h->cap, s, true);
@@ -738,7 +870,7 @@ int rsos_read_moments(rsos_handle* h, int64_t* times, int64_t* sums, int8_t* has
 {
     if (!h || cap < 0 || !n_out || !sums) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     const int rc = check_device_error(h, s);
     if (rc) return rc;
     const int n = std::min<int>(cap, (int)h->series_t.size());
@@ -765,20 +897,20 @@ int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* strea
 {
     if (!h || !host_LxL || surface < 0 || surface >= h->p.surfaces) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     const int rc = check_device_error(h, s);
     if (rc) return rc;
     const size_t n = (size_t)h->p.L * h->p.L;
-    int64_t* dev = nullptr;
-    cudaError_t e = cudaMalloc(&dev, n * 8);
+    void* dev = nullptr;
+    cudaError_t e = pool_alloc(&dev, n * 8, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return RSOS_ENOMEM;
     }
-    e = rsos::launch_heights(h->J, h->plain, surface, h->row0, dev, s);
+    e = rsos::launch_heights(h->J, h->plain, surface, h->row0, static_cast<int64_t*>(dev), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_LxL, dev, n * 8, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(dev);
     return fail_cuda(h, e);
 }
 
@@ -800,10 +932,11 @@ int rsos_free(rsos_handle* h)
 {
     if (!h) return RSOS_OK;
     int rc = RSOS_OK;
-    if (h->owns) {
-        if (cudaDeviceSynchronize() != cudaSuccess) rc = RSOS_ECUDA;
-        if (cudaFree(h->base) != cudaSuccess) rc = RSOS_ECUDA;
-    }
+    // Stream-ordered: the memory returns to the pool once the handle's last
+    // queued work is done; the host does not wait and the device is not
+    // synchronised.
+    if (h->owns && cudaFreeAsync(h->base, h->last_stream) != cudaSuccess) rc = RSOS_ECUDA;
+    if (cudaEventDestroy(h->switch_ev) != cudaSuccess) rc = RSOS_ECUDA;
     delete h;
     return rc;
 }
@@ -859,14 +992,50 @@ struct MultiWork {
     void* d_tables = nullptr;          // job tables of all rounds
     rsos::MultiJob* h_jobs = nullptr;  // pinned staging of the job tables
     unsigned int* h_err = nullptr;     // pinned: error word of each class after its last launch
+    // pooled: device buffers from the stream-ordered pool on `stream` and host
+    // staging in the calling thread's cached pinned buffer (rsos_advance,
+    // which synchronises the stream before it returns); otherwise plain
+    // allocations that live as long as a batch.
+    bool pooled = false;
+    cudaStream_t stream = nullptr;
 };
+
+// Pinned host staging of rsos_advance, cached per thread and grown on demand:
+// a call synchronises its stream before returning, so the next call on the
+// same thread may reuse it.  Kept until the process exits.
+struct PinnedCache {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+thread_local PinnedCache t_pinned;
+
+void* pinned_scratch(size_t bytes)
+{
+    if (t_pinned.bytes < bytes) {
+        if (t_pinned.p) cudaFreeHost(t_pinned.p);
+        t_pinned.p = nullptr;
+        t_pinned.bytes = 0;
+        const size_t want = std::max<size_t>(bytes, 1 << 20);
+        if (cudaHostAlloc(&t_pinned.p, want, cudaHostAllocDefault) != cudaSuccess) {
+            t_pinned.p = nullptr;
+            return nullptr;
+        }
+        t_pinned.bytes = want;
+    }
+    return t_pinned.p;
+}
 
 void multi_release(MultiWork& w)
 {
-    if (w.d_tables) cudaFree(w.d_tables);
-    if (w.d_block) cudaFree(w.d_block);
-    if (w.h_jobs) cudaFreeHost(w.h_jobs);
-    if (w.h_err) cudaFreeHost(w.h_err);
+    if (w.pooled) {
+        if (w.d_tables) cudaFreeAsync(w.d_tables, w.stream);
+        if (w.d_block) cudaFreeAsync(w.d_block, w.stream);
+    } else {
+        if (w.d_tables) cudaFree(w.d_tables);
+        if (w.d_block) cudaFree(w.d_block);
+        if (w.h_jobs) cudaFreeHost(w.h_jobs);
+        if (w.h_err) cudaFreeHost(w.h_err);
+    }
     w.d_tables = w.d_block = nullptr;
     w.h_jobs = nullptr;
     w.h_err = nullptr;
@@ -874,11 +1043,23 @@ void multi_release(MultiWork& w)
 
 // Classes, launch plans, member order and all device / pinned buffers (no
 // allocation happens later, so multi_enqueue can be captured in a graph).
+// A job whose sweep holds at least twice as many work items as the GPU has
+// worker warps keeps every warp busy alone: it runs through its own
+// single-job persistent launches (one after another), and only the smaller
+// jobs share the multi-job launches, where they run side by side.
+bool fills_gpu(const rsos_handle* h)
+{
+    const int64_t items = 4ll * h->rows * h->plan.K;
+    const int64_t workers = (int64_t)h->plan.grid * (h->plan.nthr / 32);
+    return items >= 2 * workers;
+}
+
 int multi_prepare(MultiWork& w)
 {
     for (size_t i = 0; i < w.jobs.size(); ++i) {
         rsos_handle* h = w.jobs[i];
-        if (!h->persist) {
+        // the multi-job kernel runs regular tilings only
+        if (!h->persist || h->general || fills_gpu(h)) {
             w.solo.push_back((int)i);
             continue;
         }
@@ -916,17 +1097,30 @@ int multi_prepare(MultiWork& w)
         for (int i : c.members) w.rounds = std::max(w.rounds, w.stops[i].size());
     }
     if (w.classes.empty()) return RSOS_OK;
-    if (cudaMalloc(&w.d_block, dev_bytes) != cudaSuccess) {
-        (void)cudaGetLastError();
-        w.d_block = nullptr;
-        return RSOS_ENOMEM;
-    }
     const size_t entries = w.per_round_jobs * w.rounds;
-    if (cudaMalloc(&w.d_tables, entries * sizeof(rsos::MultiJob)) != cudaSuccess ||
-        cudaHostAlloc((void**)&w.h_jobs, entries * sizeof(rsos::MultiJob), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&w.h_err, w.classes.size() * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return RSOS_ENOMEM;
+    if (w.pooled) {
+        const size_t tables = align256(entries * sizeof(rsos::MultiJob));
+        unsigned char* host = static_cast<unsigned char*>(pinned_scratch(tables + 256));
+        if (!host || pool_alloc(&w.d_block, dev_bytes, w.stream) != cudaSuccess ||
+            pool_alloc(&w.d_tables, entries * sizeof(rsos::MultiJob), w.stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return RSOS_ENOMEM;
+        }
+        w.h_jobs = reinterpret_cast<rsos::MultiJob*>(host);
+        w.h_err = reinterpret_cast<unsigned int*>(host + tables);
+    } else {
+        if (cudaMalloc(&w.d_block, dev_bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            w.d_block = nullptr;
+            return RSOS_ENOMEM;
+        }
+        if (cudaMalloc(&w.d_tables, entries * sizeof(rsos::MultiJob)) != cudaSuccess ||
+            cudaHostAlloc((void**)&w.h_jobs, entries * sizeof(rsos::MultiJob), cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void**)&w.h_err, w.classes.size() * sizeof(unsigned int), cudaHostAllocDefault) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            return RSOS_ENOMEM;
+        }
     }
     unsigned char* cur = static_cast<unsigned char*>(w.d_block);
     rsos::MultiJob* dj = static_cast<rsos::MultiJob*>(w.d_tables);
@@ -1069,9 +1263,12 @@ extern "C" int rsos_advance(rsos_handle* const* jobs, const int64_t* t_target, i
     }
     cudaStream_t s = as_stream(stream);
     for (rsos_handle* h : w.jobs) {
+        use_stream(h, stream);
         const int rc = measure_due(h, s);  // a measurement due at the current time
         if (rc) return rc;
     }
+    w.pooled = true;
+    w.stream = s;
     int rc = multi_prepare(w);
     if (rc == RSOS_OK) rc = multi_enqueue(w, s, false, nullptr);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -1176,6 +1373,7 @@ int rsos_batch_run(rsos_batch* b, void* stream)
     if (b->queued) return RSOS_EBUSY;
     cudaStream_t s = as_stream(stream);
     MultiWork& w = b->w;
+    for (rsos_handle* h : w.jobs) use_stream(h, stream);  // before capture: no cross-stream waits inside
     int rc = RSOS_OK;
     if (!b->prepared) {
         w.stops.clear();
@@ -1280,6 +1478,7 @@ int rsos_batch_free(rsos_batch* b)
     for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
     multi_release(b->w);
     for (rsos_handle* h : b->w.jobs) {
+        h->last_stream = nullptr;  // the device is idle: release without the run's stream
         const int r = rsos_free(h);
         if (r) rc = r;
     }
@@ -1337,7 +1536,9 @@ extern "C" int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_par
     *tuned = *params;
     if (us_per_sweep) *us_per_sweep = 0.0;
     const Layout l = layout_of(params);
-    if (!l.persist_on) return RSOS_OK;  // nothing to choose outside the persistent engine
+    // nothing to choose outside the regular persistent engine ((+1) tilings
+    // keep the automatic geometry)
+    if (!l.persist_on || params->tiling == 1) return RSOS_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1464,7 +1665,7 @@ extern "C" int rsos_snapshot(rsos_handle* h, void* host_buf, size_t bytes, void*
     if (!h || !host_buf) return RSOS_EINVAL;
     if (h->sticky) return h->sticky;
     if (bytes < snapshot_size(h)) return RSOS_ENOMEM;
-    cudaStream_t s = as_stream(stream);
+    cudaStream_t s = use_stream(h, stream);
     int rc = check_device_error(h, s);
     if (rc) return rc;
     unsigned char* out = static_cast<unsigned char*>(host_buf);
@@ -1552,7 +1753,7 @@ extern "C" int rsos_restore(const void* host_buf, size_t bytes, void* dev_buf, s
     // t = 0: a job resumed at t has completed t sweeps of every row.
     std::vector<unsigned long long> done;
     if (e == cudaSuccess && h->persist) {
-        done.assign((size_t)4 * h->J.nT, (unsigned long long)hd.t * (unsigned long long)h->plan.K);
+        done.assign((size_t)4 * h->rows, (unsigned long long)hd.t * (unsigned long long)h->plan.K);
         e = cudaMemcpyAsync(h->done, done.data(), done.size() * 8, cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

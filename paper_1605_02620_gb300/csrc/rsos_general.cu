@@ -10,6 +10,7 @@
 // k = floor(u a / 2^16) of a 16-bit u, kx = k mod w, ky = k div w.
 #include <mutex>
 
+#include "rsos_gen_sched.cuh"
 #include "rsos_general.cuh"
 #include "rsos_launch.h"
 
@@ -138,6 +139,60 @@ __global__ void __launch_bounds__(256) general_phase_kernel(JobDev J, GenTiling 
         general_activate<N, WT, false>(J, G, sm, tid, nthr, tx, ty, wp, t, p, q, ox, oy, -1);
 }
 
+// Persistent dataflow engine on a (+1) tiling: the worker loop of the
+// regular persistent engine (rsos_persist.cuh) over the items and
+// dependencies of rsos_gen_sched.cuh, each lane activating its tile's
+// sub-tile with the extents of that tile (general_activate).  Every warp owns
+// windows for the widest half of either axis.
+template <int N, typename WT>
+__global__ void __launch_bounds__(32 * kGenPersistWarps, 4) general_persistent_kernel(GenPersistArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int B = bits_for_step(N);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t slots = (size_t)(A.G.max_w + 2) * (size_t)(A.G.max_h + 2);
+    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * slots * B * 32;
+    const int NWP = A.J.NWP;
+    const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
+    const int lanes_used = (32 / NWP) * NWP;
+    const int ny = A.S.y.n;
+    unsigned long long next = 0;
+    if (lane == 0) next = atomicAdd(A.ticket, 1ull);
+    GenSweepCtx sc;
+    sc.t = 0xffffffffu;
+    GenOrigin o{};
+    for (;;) {
+        const unsigned long long tk = __shfl_sync(0xffffffffu, next, 0);
+        if (tk >= A.n_tickets) break;
+        const uint32_t t_before = sc.t;
+        const Item it = gen_item_of_ticket(A.S, tk, A.t0, &sc);
+        if (sc.t != t_before) o = gen_locate_origin_site(A.J.L, A.G, sc.ctl.ox, sc.ctl.oy);
+        Dep dep;
+        int waited = 1;
+        if (lane < 4 && gen_item_dep(A.S, it, lane, sc, &dep)) {
+            waited = wait_at_least(A.done + (size_t)dep.p * ny + dep.r, dep.target, A.err, A.budget_ns);
+            if (!waited) atomicCAS(A.err, 0u, kPersistTimeout);
+        }
+        if (!__all_sync(0xffffffffu, waited)) break;
+        __syncwarp();  // orders lanes 0..3's acquire loads before every lane's staging
+        if (lane == 0) next = atomicAdd(A.ticket, 1ull);  // overlaps with the work below
+        const int q = sc.ctl.perm[it.p];
+        if (lane < lanes_used) {
+            for (int k = 0; k < A.TPL; ++k) {
+                const int tx = it.c * A.CW + k * (32 / NWP) + lane_tile;
+                if (tx >= A.G.x.n) break;
+                if (q == o.q && tx == o.tx && it.r == o.ty)
+                    general_activate<N, WT, true>(A.J, A.G, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q, sc.ctl.ox,
+                                                  sc.ctl.oy, o.k);
+                else
+                    general_activate<N, WT, false>(A.J, A.G, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q, sc.ctl.ox,
+                                                   sc.ctl.oy, -1);
+            }
+        }
+        publish_done(A.done + (size_t)it.p * ny + it.r, lane);
+    }
+}
+
 constexpr size_t kMaxDynamicSmem = 227 * 1024;  // largest dynamic shared memory of a block
 
 // Allows general_phase_kernel<N, WT> the largest dynamic shared memory, once
@@ -217,7 +272,94 @@ cudaError_t launch_general_t(const JobDev& J, const GenTiling& G, uint32_t t, in
     return cudaGetLastError();
 }
 
+template <int N, typename WT>
+cudaError_t plan_gen_persist_t(const JobDev& J, const GenTiling& G, int block_tiles, int phase_lag, PersistPlan* P)
+{
+    constexpr int B = bits_for_step(N);
+    const size_t per_thread = (size_t)(G.max_w + 2) * (size_t)(G.max_h + 2) * B * sizeof(WT);
+    P->CW = block_tiles;
+    if (P->CW < 1) return cudaErrorInvalidConfiguration;
+    P->K = (G.x.n + P->CW - 1) / P->CW;
+    P->nthr = 32 * kGenPersistWarps;
+    P->smem = per_thread * (size_t)P->nthr;
+    if (P->smem > kMaxDynamicSmem) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(general_persistent_kernel<N, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P->smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, general_persistent_kernel<N, WT>, P->nthr, P->smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    P->grid = per_sm * sms;
+    // phase lag as for the regular engine: 1.5 x the items in flight (two
+    // per worker warp) per slot of 4K items, at most a third of the rows
+    const int per_slot = 4 * P->K;
+    const int workers = P->grid * kGenPersistWarps;
+    int D = (int)(1.5 * 2.0 * workers / per_slot);
+    const int dmax = G.y.n / 3 > 2 ? G.y.n / 3 : 2;
+    if (D > dmax) D = dmax;
+    if (D < 2) D = 2;
+    if (phase_lag >= 2) D = phase_lag;
+    P->D = D;
+    (void)J;
+    return cudaSuccess;
+}
+
+template <int N, typename WT>
+cudaError_t launch_gen_persist_t(const GenPersistArgs& A, const PersistPlan& P, cudaStream_t s)
+{
+    GenPersistArgs a = A;
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void*)general_persistent_kernel<N, WT>, dim3(P.grid), dim3(P.nthr), args,
+                                       P.smem, s);
+}
+
 }  // namespace
+
+cudaError_t plan_gen_persist(const JobDev& J, const GenTiling& G, int words_per_thread, int block_tiles,
+                             int phase_lag, PersistPlan* out)
+{
+#define RSOS_CASE(NN)                                                                                     \
+    case NN:                                                                                              \
+        return words_per_thread == 2 ? plan_gen_persist_t<NN, uint64_t>(J, G, block_tiles, phase_lag, out) \
+                                     : plan_gen_persist_t<NN, uint32_t>(J, G, block_tiles, phase_lag, out);
+    switch (J.N) {
+        RSOS_CASE(1)
+        RSOS_CASE(2)
+        RSOS_CASE(3)
+        RSOS_CASE(4)
+        RSOS_CASE(5)
+        RSOS_CASE(6)
+        RSOS_CASE(7)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef RSOS_CASE
+}
+
+cudaError_t launch_gen_persist(int N, int words_per_thread, const GenPersistArgs& A, const PersistPlan& P,
+                               cudaStream_t s)
+{
+#define RSOS_CASE(NN)                                                                   \
+    case NN:                                                                            \
+        return words_per_thread == 2 ? launch_gen_persist_t<NN, uint64_t>(A, P, s)      \
+                                     : launch_gen_persist_t<NN, uint32_t>(A, P, s);
+    switch (N) {
+        RSOS_CASE(1)
+        RSOS_CASE(2)
+        RSOS_CASE(3)
+        RSOS_CASE(4)
+        RSOS_CASE(5)
+        RSOS_CASE(6)
+        RSOS_CASE(7)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef RSOS_CASE
+}
 
 cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_per_thread, uint32_t t, int p, int q,
                                  int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s,

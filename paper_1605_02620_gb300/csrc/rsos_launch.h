@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "rsos_device.cuh"
+#include "rsos_gen_sched.cuh"
 #include "rsos_general.cuh"
 #include "rsos_persist.cuh"
 
@@ -24,6 +25,22 @@ cudaError_t launch_phase_general(const JobDev& J, const GenTiling& G, int words_
                                  int ox, int oy, const GenOrigin& o, size_t smem_budget, cudaStream_t s,
                                  int* n_launches);
 
+// Persistent engine on a (+1) tiling (rsos_gen_sched.cuh): the worker loop
+// of the regular persistent engine over the tiling's rows.
+constexpr int kGenPersistWarps = 3;  // warps per block
+struct GenPersistArgs {
+    JobDev J;
+    GenTiling G;
+    GenSchedGeom S;
+    unsigned long long* done;      // [4][ny] completion counters
+    unsigned long long* ticket;    // next ticket (zeroed before each launch)
+    unsigned int* err;             // error word
+    uint32_t t0;                   // first sweep of the launch
+    unsigned long long n_tickets;  // items of the launch, < 2^31
+    int CW, TPL;                   // tiles per item, tiles per lane
+    long long budget_ns;           // time budget of every single wait
+};
+
 #define RSOS_DECLARE_SX(SX)                                                                          \
     cudaError_t launch_phase_s##SX(const JobDev& J, int words_per_thread, uint32_t t, int p, int q,  \
                                    int ox, int oy, const Origin00& o, size_t smem_budget,           \
@@ -43,6 +60,12 @@ struct PersistPlan {
     int CW, K, D, nthr, grid;
     size_t smem;
 };
+// (+1) tilings: the same plan and a cooperative launch of
+// general_persistent_kernel (rsos_general.cu).
+cudaError_t plan_gen_persist(const JobDev& J, const GenTiling& G, int words_per_thread, int block_tiles,
+                             int phase_lag, PersistPlan* out);
+cudaError_t launch_gen_persist(int N, int words_per_thread, const GenPersistArgs& A, const PersistPlan& P,
+                               cudaStream_t s);
 // phase_lag >= 2 fixes the lag; 0 lets the plan choose it.
 cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, int phase_lag,
                          PersistPlan* out);

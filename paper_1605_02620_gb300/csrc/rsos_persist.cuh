@@ -33,6 +33,7 @@ RSOS_HD constexpr int persist_warps_per_block(int SX, int B, int word_bytes)
 
 template <int N, typename WT, int SX>
 struct PersistCfg {
+    static constexpr int SLOTS = (SX + 2) * (SX + 2);  // window slots per thread
     static constexpr int WPB = persist_warps_per_block(SX, bits_for_step(N), (int)sizeof(WT));
     static constexpr int BLOCK = 32 * WPB;
     static constexpr int MIN_BLOCKS = 12 / WPB;  // caps registers at ~170 per thread
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     constexpr int T = 2 * SX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * (SX + 2) * (SX + 2) * B * 32;
+    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * PersistCfg<N, WT, SX>::SLOTS * B * 32;
     const int NWP = A.J.NWP;
     const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
     const int lanes_used = (32 / NWP) * NWP;
@@ -168,6 +169,10 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
             if (!waited) atomicCAS(A.err, 0u, kPersistTimeout);
         }
         if (!__all_sync(0xffffffffu, waited)) break;
+        // Lanes 0..3 took the acquire loads; the warp barrier orders them
+        // before every lane's staging loads (vote.sync alone is not
+        // documented to order memory).
+        __syncwarp();
         if (lane == 0) next = atomicAdd(A.ticket, 1ull);  // overlaps with the work below
         const int q = ctl.perm[it.p];
         if (lane < lanes_used) {
@@ -175,11 +180,11 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
                 const int tx = it.c * A.CW + k * (32 / NWP) + lane_tile;
                 if (tx >= A.J.nT) break;
                 if (q == o.q && tx == o.tx && it.r == o.ty) {
-                    activate_subtile<N, WT, SX, true, true, 32>(A.J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q,
-                                                                ctl.ox, ctl.oy, o.k);
+                    activate_subtile<N, WT, SX, true, true, 32, true>(A.J, sm_w, lane, 32, tx, it.r, wp, it.t,
+                                                                          it.p, q, ctl.ox, ctl.oy, o.k);
                 } else {
-                    activate_subtile<N, WT, SX, false, true, 32>(A.J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q,
-                                                                 ctl.ox, ctl.oy, -1);
+                    activate_subtile<N, WT, SX, false, true, 32, true>(A.J, sm_w, lane, 32, tx, it.r, wp, it.t,
+                                                                           it.p, q, ctl.ox, ctl.oy, -1);
                 }
             }
         }
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
     constexpr int T = 2 * SX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * (SX + 2) * (SX + 2) * B * 32;
+    WT* sm_w = reinterpret_cast<WT*>(smem_raw) + (size_t)warp * PersistCfg<N, WT, SX>::SLOTS * B * 32;
     int next_job = 0;
     unsigned long long next_tk = 0;
     int have = 0;
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
         J.phase_order = mj.J.phase_order;
         J.seed_lo = mj.J.seed_lo;
         J.seed_hi = mj.J.seed_hi;
+        J.rk = mj.J.rk;  // the job's Philox round keys, from its table entry
         const SchedGeom G = mj.G;
         const int CW = mj.CW, TPL = mj.TPL;
         if (j != sc_job) sc.t = 0xffffffffu;  // the cached sweep belongs to another job
@@ -279,6 +285,7 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
             if (!waited) atomicCAS(M.err, 0u, kPersistTimeout);
         }
         if (!__all_sync(0xffffffffu, waited)) break;
+        __syncwarp();  // orders lanes 0..3's acquire loads before every lane's staging
         if (lane == 0) have = take_multi_ticket(M, &next_job, &next_tk);
         const int NWP = J.NWP;
         const int lane_tile = lane / NWP, wp = lane - lane_tile * NWP;
@@ -288,11 +295,11 @@ __global__ void __launch_bounds__(PersistCfg<N, WT, SX>::BLOCK, PersistCfg<N, WT
                 const int tx = it.c * CW + k * (32 / NWP) + lane_tile;
                 if (tx >= J.nT) break;
                 if (q == o.q && tx == o.tx && it.r == o.ty) {
-                    activate_subtile<N, WT, SX, true, true, 32, false>(J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p, q,
-                                                                       ctl.ox, ctl.oy, o.k);
+                    activate_subtile<N, WT, SX, true, true, 32, true>(J, sm_w, lane, 32, tx, it.r, wp, it.t,
+                                                                           it.p, q, ctl.ox, ctl.oy, o.k);
                 } else {
-                    activate_subtile<N, WT, SX, false, true, 32, false>(J, sm_w, lane, 32, tx, it.r, wp, it.t, it.p,
-                                                                        q, ctl.ox, ctl.oy, -1);
+                    activate_subtile<N, WT, SX, false, true, 32, true>(J, sm_w, lane, 32, tx, it.r, wp, it.t,
+                                                                            it.p, q, ctl.ox, ctl.oy, -1);
                 }
             }
         }

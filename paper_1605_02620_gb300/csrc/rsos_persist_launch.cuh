@@ -12,7 +12,7 @@ cudaError_t plan_persist_t(const JobDev& J, int block_tiles, int phase_lag, Pers
 {
     constexpr int B = bits_for_step(N);
     constexpr int WPB = PersistCfg<N, WT, SX>::WPB;
-    const size_t per_thread = (size_t)(SX + 2) * (SX + 2) * B * sizeof(WT);
+    const size_t per_thread = (size_t)PersistCfg<N, WT, SX>::SLOTS * B * sizeof(WT);
     P->CW = block_tiles;  // TPL * (32 / NWP), fixed by the job layout
     if (P->CW < 1) return cudaErrorInvalidConfiguration;
     P->K = (J.nT + P->CW - 1) / P->CW;
@@ -67,7 +67,7 @@ cudaError_t plan_multi_t(int* grid, int* block, size_t* smem)
     constexpr int B = bits_for_step(N);
     constexpr int WPB = PersistCfg<N, WT, SX>::WPB;
     *block = 32 * WPB;
-    *smem = (size_t)(SX + 2) * (SX + 2) * B * sizeof(WT) * (size_t)(*block);
+    *smem = (size_t)PersistCfg<N, WT, SX>::SLOTS * B * sizeof(WT) * (size_t)(*block);
     cudaError_t e = cudaFuncSetAttribute(persistent_multi_kernel<N, WT, SX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     if (e != cudaSuccess) return e;

@@ -322,3 +322,114 @@ long long probe_gen_plan_check(int L, int Tx, int Ty, int NWP, int wbytes, int n
     return bad;
 }
 }
+
+// Scheduling rules of the persistent engine on (+1) tilings.
+#include "rsos_gen_sched.cuh"
+
+extern "C" {
+
+// g8: L, Tx, Ty, K, D, phase_order, seed_lo, seed_hi
+static rsos::GenSchedGeom make_gen_geom(const int* g8)
+{
+    rsos::GenSchedGeom g;
+    g.L = g8[0];
+    g.y = rsos::gen_axis(g8[0], g8[2]);
+    g.Px = rsos::gen_period(g8[0], g8[1]);
+    g.Py = rsos::gen_period(g8[0], g8[2]);
+    g.K = g8[3]; g.D = g8[4]; g.phase_order = g8[5];
+    g.seed_lo = (uint32_t)g8[6]; g.seed_hi = (uint32_t)g8[7];
+    return g;
+}
+
+void probe_gen_item(const int* g8, uint64_t ticket, uint32_t t0, int* out4)
+{
+    rsos::GenSweepCtx c;
+    c.t = 0xffffffffu;
+    const rsos::Item it = rsos::gen_item_of_ticket(make_gen_geom(g8), ticket, t0, &c);
+    out4[0] = (int)it.t; out4[1] = it.p; out4[2] = it.r; out4[3] = it.c;
+}
+
+int probe_gen_deps(const int* g8, const int* item4, int64_t* out12)
+{
+    rsos::Item it;
+    it.t = (uint32_t)item4[0]; it.p = item4[1]; it.r = item4[2]; it.c = item4[3];
+    rsos::Dep d[4];
+    const int n = rsos::gen_item_deps(make_gen_geom(g8), it, d);
+    for (int k = 0; k < n; ++k) {
+        out12[3 * k] = d[k].p; out12[3 * k + 1] = d[k].r; out12[3 * k + 2] = (int64_t)d[k].target;
+    }
+    return n;
+}
+}
+
+// Bulk staging runs (slot_runs, staged_slot) against window_index: for every
+// origin, set, tile row, warp group start tx0 (a multiple of 32), group size
+// and staged slot, the runs cover the group's tiles in order, each tile's
+// record offset is the one window_index gives, and every run lies inside the
+// lattice.  Returns mismatches; *n_checked = records checked.
+template <int SX>
+static long long bulk_check(int L, int NW, int B, long long* n_checked)
+{
+    constexpr int T = 2 * SX;
+    rsos::JobDev J{};
+    J.L = L; J.T = T; J.nT = L / T; J.NW = NW; J.B = B;
+    const long long total = (long long)B * L * L * NW;
+    const long long rec_words = (long long)B * NW;
+    long long bad = 0, n_rec = 0;
+    const int NS = (SX + 2) * (SX + 2) - 4;
+    for (int oy = 0; oy < T; ++oy)
+        for (int ox = 0; ox < T; ++ox)
+            for (int q = 0; q < 4; ++q)
+                for (int ty = 0; ty < J.nT; ++ty)
+                    for (int tx0 = 0; tx0 < J.nT; tx0 += 32) {
+                        const int nmax = J.nT - tx0 < 32 ? J.nT - tx0 : 32;
+                        for (int n = 1; n <= nmax; ++n)
+                            for (int m = 0; m < NS; ++m) {
+                                int jj, ii;
+                                rsos::staged_slot<SX>(m, jj, ii);
+                                if ((jj == 0 || jj == SX + 1) && (ii == 0 || ii == SX + 1)) { ++bad; continue; }
+                                const rsos::SlotRuns r = rsos::slot_runs<SX>(J, tx0, n, ty, q & 1, q >> 1, ox, oy, jj, ii);
+                                if (r.first[0] != 0 || r.count[0] < 0 || r.count[1] < 0 ||
+                                    r.first[1] != r.count[0] || r.count[0] + r.count[1] != n) { ++bad; continue; }
+                                for (int u = 0; u < 2; ++u) {
+                                    if (r.count[u] == 0) continue;
+                                    const long long lo = (long long)r.word[u];
+                                    const long long hi = lo + (long long)r.count[u] * rec_words;
+                                    if (lo < 0 || hi > total) ++bad;
+                                    for (int i = 0; i < r.count[u]; ++i) {
+                                        rsos::WindowIndex<SX> wi;
+                                        rsos::window_index<SX>(J, tx0 + r.first[u] + i, ty, q & 1, q >> 1, ox, oy, 0, wi);
+                                        const long long want = (long long)(wi.row[jj] + wi.col[ii]);
+                                        bad += (lo + (long long)i * rec_words != want) ? 1 : 0;
+                                        ++n_rec;
+                                    }
+                                }
+                            }
+                    }
+    // every non-corner slot exactly once
+    int seen[(SX + 2) * (SX + 2)] = {0};
+    for (int m = 0; m < NS; ++m) {
+        int jj, ii;
+        rsos::staged_slot<SX>(m, jj, ii);
+        if (jj < 0 || jj > SX + 1 || ii < 0 || ii > SX + 1) { ++bad; continue; }
+        ++seen[jj * (SX + 2) + ii];
+    }
+    for (int jj = 0; jj < SX + 2; ++jj)
+        for (int ii = 0; ii < SX + 2; ++ii) {
+            const bool corner = (jj == 0 || jj == SX + 1) && (ii == 0 || ii == SX + 1);
+            bad += seen[jj * (SX + 2) + ii] != (corner ? 0 : 1) ? 1 : 0;
+        }
+    *n_checked = n_rec;
+    return bad;
+}
+
+extern "C" long long probe_bulk_check(int L, int T, int NW, int B, long long* n_checked)
+{
+    switch (T) {
+        case 2: return bulk_check<1>(L, NW, B, n_checked);
+        case 4: return bulk_check<2>(L, NW, B, n_checked);
+        case 8: return bulk_check<4>(L, NW, B, n_checked);
+        case 16: return bulk_check<8>(L, NW, B, n_checked);
+        default: return -1;
+    }
+}

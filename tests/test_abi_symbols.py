@@ -69,15 +69,20 @@ def test_restore_rejects_foreign_bytes_without_gpu():
 
 
 def test_general_tiling_params_validated_without_gpu():
-    """(+1) tilings (section III.C): impossible axes, the persistent engine and
-    single-surface jobs are rejected before any device work."""
+    """(+1) tilings (section III.C): impossible axes, the persistent engine
+    where its windows do not fit a block, and single-surface jobs are rejected
+    before any device work."""
     import paper_1605_02620_gb300 as R
     import pytest
     ok = dict(L=64, N=1, surfaces=64, tile=(6, 10), tiling=1)
     assert R.rsos_required_bytes(R.rsos_params(**ok)) >= 2 * 64 * 64 * 8
     assert R.rsos_required_bytes(R.rsos_params(L=9605, N=1, surfaces=64, tile=(6, 10), tiling=1)) >= 2 * 9605 ** 2 * 8
     assert R.rsos_required_bytes(R.rsos_params(L=61, N=4, surfaces=64, tile=30, tiling=1)) > 0
-    for bad in [dict(ok, L=10, tile=7), dict(ok, tile=(1, 10)), dict(ok, tile=(6, 31)), dict(ok, engine=2),
+    # the persistent engine runs 6(+1) x 10(+1); 30(+1) windows of 4 bit
+    # planes are too large for its blocks
+    assert R.rsos_required_bytes(R.rsos_params(**dict(ok, engine=2))) > 0
+    for bad in [dict(ok, L=10, tile=7), dict(ok, tile=(1, 10)), dict(ok, tile=(6, 31)),
+                dict(L=61, N=4, surfaces=64, tile=30, tiling=1, engine=2),
                 dict(ok, surfaces=1), dict(ok, tiling=2), dict(ok, L=5, tile=6), dict(ok, N=8)]:
         with pytest.raises(R.RsosError):
             R.rsos_required_bytes(R.rsos_params(**bad))

@@ -30,6 +30,51 @@ def test_general_tiling_matches_oracle(L, N, S, T, order, t_end):
     assert_parity(L, N, S, T, seed=41 + L + N, order=order, times=times, t_end=t_end, tiling=1)
 
 
+@pytest.mark.parametrize("L,N,S,T,order,t_end", [
+    (64, 1, 64, (6, 10), 0, 30),
+    (64, 3, 32, (6, 10), 0, 25),
+    (37, 2, 96, (4, 5), 0, 30),
+    (50, 1, 128, (8, 8), 1, 30),
+    (27, 7, 64, (3, 9), 0, 20),
+    (13, 2, 2048, (2, 2), 0, 12),
+    (9, 1, 64, (2, 3), 0, 40),
+    (130, 1, 64, (6, 10), 0, 24),   # 13 tile rows
+])
+def test_persistent_engine_on_general_tilings_matches_oracle(L, N, S, T, order, t_end):
+    """The persistent dataflow engine on (+1) tilings (its own work order:
+    tile rows T or T + 1 high, the origin anywhere in the pattern's period)
+    against the oracle, bit for bit, on the tilings above, down to one or
+    two tile rows per axis."""
+    times = sorted({0, 1, 3, t_end // 2, t_end})
+    assert_parity(L, N, S, T, seed=41 + L + N, order=order, times=times, t_end=t_end, tiling=1, engine=2)
+
+
+def test_persistent_and_phase_engines_agree_at_L9605():
+    kw = dict(L=9605, N=1, S=64, T=(6, 10), seed=21, times=[0, 1, 5, 12], t_end=12, height_lanes=[0, 63],
+              tiling=1)
+    a = gpu_run(engine=1, **kw)
+    b = gpu_run(engine=2, **kw)
+    assert (a[1] == b[1]).all() and (a[2] == b[2]).all()
+    for j in (0, 63):
+        assert np.array_equal(a[4][j], b[4][j]), j
+
+
+def test_persistent_engine_wait_timeout_on_general_tiling():
+    p = R.rsos_params(L=130, N=1, surfaces=64, tile=(6, 10), seed=2, engine=2, tiling=1, series_capacity=4)
+    h = R.rsos_init(p)
+    try:
+        R.rsos_sweep(h, 3)
+        s1, s2, _, _ = R.rsos_width(h, 64)
+        assert R.rsos_selftest_timeout(h, 20_000_000) == R.RSOS_ETIMEOUT
+        # the lattice is untouched and the handle keeps working
+        t1, t2, _, _ = R.rsos_width(h, 64)
+        assert (s1 == t1).all() and (s2 == t2).all()
+        R.rsos_sweep(h, 2)
+        assert R.rsos_time(h) == 5
+    finally:
+        R.rsos_free(h)
+
+
 @pytest.mark.parametrize("L,N,S,T", [(256, 1, 64, 8), (128, 2, 32, 4), (64, 5, 64, 16)])
 def test_divisible_tiles_equal_the_regular_engines(L, N, S, T):
     kw = dict(L=L, N=N, S=S, T=T, seed=7, times=[0, 3, 11], t_end=11, height_lanes=[0, S - 1])

@@ -36,7 +36,9 @@ def test_served_results_equal_solo_runs():
             for k, (L, N, t) in enumerate([(128, 1, 30), (64, 2, 50), (256, 1, 20), (64, 4, 40), (128, 3, 25),
                                            (96, 1, 60), (64, 1, 10), (128, 2, 35), (256, 2, 15), (64, 3, 45)])]
     budget = 3 * R.rsos_required_bytes(R.rsos_params(L=256, N=2, surfaces=64, series_capacity=2))
-    rep = Server(hbm_budget=budget, epoch_s=0.002).run(reqs)
+    # epochs of a few sweeps per job, so that a job stays resident over several
+    # epochs and later arrivals join it
+    rep = Server(hbm_budget=budget, epoch_s=1e-5, rate_guess=1e11).run(reqs)
     assert len(rep.results) == len(reqs)
     by_id = {r.rid: r for r in rep.results}
     for q in reqs:
@@ -46,3 +48,9 @@ def test_served_results_equal_solo_runs():
         assert r.finished >= r.admitted >= q.arrival - 1e-9
     s = rep.summary()
     assert s["jobs"] == len(reqs) and s["latency_p99_s"] >= s["latency_p50_s"]
+    # continuous batching: jobs were resident together, and some request was
+    # admitted while another job was already resident (it joined the running
+    # work instead of waiting for it to drain)
+    assert rep.max_active > 1
+    res = rep.results
+    assert any(a.admitted < b.admitted < a.finished for a in res for b in res if a is not b)

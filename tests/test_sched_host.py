@@ -36,6 +36,8 @@ def probe(tmp_path_factory):
     lib.probe_order_entry.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ip]
     lib.probe_item.argtypes = [ip, ctypes.c_uint64, ctypes.c_uint32, ip]
     lib.probe_deps.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_int64)]
+    lib.probe_gen_item.argtypes = [ip, ctypes.c_uint64, ctypes.c_uint32, ip]
+    lib.probe_gen_deps.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_int64)]
     return lib
 
 
@@ -144,6 +146,104 @@ def test_schedule_is_sound(probe, L, T, CW, D, seed, order):
         ox, oy, perm = O.control(p_, t)
         txs = [tx for tx in range(c * CW, min(nT, (c + 1) * CW))]
         foot[(t, p, r, c)] = _footprint(L, T, ox, oy, perm[p], r, txs)
+    seq = sorted(items, key=lambda it: (it[0], it[1]))
+    for i, a in enumerate(seq):
+        wa, ra = foot[a]
+        for b in seq[i + 1:]:
+            wb, rb = foot[b]
+            if not (wa & rb or ra & wb):
+                continue
+            assert (a[0], a[1]) != (b[0], b[1]), ("same-phase conflict", a, b)
+            assert depends(b, a), (b, "must depend on", a)
+
+
+def _gen_footprint(L, Tx, Ty, ox, oy, q, ty, txs):
+    """Sites written (sub-tile) and touched (sub-tile + halo) by an item of a
+    (+1) tiling, from the oracle's own tiling geometry (axis_half)."""
+    qx, qy = q & 1, q >> 1
+    v0, sh = O.axis_half(L, Ty, ty, qy)
+    wr, rd = set(), set()
+    for tx in txs:
+        u0, sw = O.axis_half(L, Tx, tx, qx)
+        for ky in range(-1, sh + 1):
+            for kx in range(-1, sw + 1):
+                inside = 0 <= kx < sw and 0 <= ky < sh
+                edge = (kx in (-1, sw)) != (ky in (-1, sh))
+                if not inside and not edge:
+                    continue
+                site = ((ox + u0 + kx) % L, (oy + v0 + ky) % L)
+                rd.add(site)
+                if inside:
+                    wr.add(site)
+    return wr, rd
+
+
+@pytest.mark.parametrize("L,Tx,Ty,CW,D,seed,order", [
+    (13, 3, 4, 2, 2, 1, 0), (20, 6, 4, 1, 2, 2, 0), (17, 4, 2, 2, 3, 3, 0), (14, 2, 3, 3, 2, 4, 1),
+    (22, 6, 10, 1, 2, 5, 0), (16, 8, 8, 1, 2, 6, 0), (11, 2, 2, 2, 2, 7, 0), (25, 4, 6, 2, 3, 8, 0),
+])
+def test_general_schedule_is_sound(probe, L, Tx, Ty, CW, D, seed, order):
+    """The (+1)-tiling schedule: every item once, dependencies earlier in
+    ticket order, per-row completion counters monotone, and every pair of
+    conflicting activations (a common site, one of them writing it) ordered
+    by a dependency path in sequential (t, p) order.  Footprints come from
+    the oracle's tiling geometry and control draw, not from the product."""
+    nx, ny = L // Tx, L // Ty
+    K = -(-nx // CW)
+    n_sweeps = 6
+    g8 = np.array([L, Tx, Ty, K, D, order, seed, 0], dtype=np.int32)
+    gp = g8.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    n = 4 * ny * K
+    items, ticket_of = [], {}
+    out = np.zeros(4, dtype=np.int32)
+    for tk in range(n_sweeps * n):
+        probe.probe_gen_item(gp, tk, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        it = tuple(int(v) for v in out)
+        assert it not in ticket_of
+        ticket_of[it] = tk
+        items.append(it)
+    assert set(ticket_of) == {(t, p, r, c) for t in range(n_sweeps) for p in range(4)
+                              for r in range(ny) for c in range(K)}
+    deps = {}
+    buf = np.zeros(12, dtype=np.int64)
+    for it in items:
+        a = np.array(it, dtype=np.int32)
+        k = probe.probe_gen_deps(gp, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        ds = set()
+        for m in range(k):
+            p2, r2, target = int(buf[3 * m]), int(buf[3 * m + 1]), int(buf[3 * m + 2])
+            assert target % K == 0 and 0 <= r2 < ny
+            td = target // K - 1
+            assert td <= it[0]
+            for t2 in range(td + 1):
+                for c2 in range(K):
+                    ds.add((t2, p2, r2, c2))
+        for d in ds:
+            assert ticket_of[d] < ticket_of[it], (it, d)
+        deps[it] = ds
+    index = {it: i for i, it in enumerate(items)}
+    reach = [0] * len(items)
+    for i, it in enumerate(items):
+        m = 0
+        for d in deps[it]:
+            j = index[d]
+            m |= reach[j] | (1 << j)
+        reach[i] = m
+
+    def depends(a, b):
+        return bool((reach[index[a]] >> index[b]) & 1)
+
+    for (t, p, r, c) in items:
+        if t + 1 < n_sweeps:
+            for c2 in range(K):
+                assert depends((t + 1, p, r, c), (t, p, r, c2))
+    p_ = O.Params(L=L, N=1, Tx=Tx, Ty=Ty, phase_order=order, seed=seed, tiling=1)
+    foot = {}
+    for (t, p, r, c) in items:
+        ox, oy, perm = O.control(p_, t)
+        txs = [tx for tx in range(c * CW, min(nx, (c + 1) * CW))]
+        foot[(t, p, r, c)] = _gen_footprint(L, Tx, Ty, ox, oy, perm[p], r, txs)
     seq = sorted(items, key=lambda it: (it[0], it[1]))
     for i, a in enumerate(seq):
         wa, ra = foot[a]
