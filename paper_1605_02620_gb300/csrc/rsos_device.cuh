@@ -115,66 +115,6 @@ RSOS_HD void window_index(const JobDev& J, int tx, int ty, int qx, int qy, int o
     }
 }
 
-// Bulk staging of a warp's windows (persistent engine, one thread per tile
-// and whole site records): for one window slot (jj, ii), the records of the
-// warp's consecutive tiles tx0 .. tx0 + n - 1 (n <= 32) of tile row ty are
-// consecutive in the class-interleaved layout, except where the slot's column
-// wraps around the row; so a slot is at most two contiguous runs of records.
-struct SlotRuns {
-    size_t word[2];  // word offset (plane 0) of each run in the lattice
-    int first[2];    // first tile (0 .. n-1) of each run
-    int count[2];    // records of each run (either may be 0)
-};
-
-template <int SX>
-RSOS_HD SlotRuns slot_runs(const JobDev& J, int tx0, int n, int ty, int qx, int qy, int ox, int oy, int jj, int ii)
-{
-    constexpr int T = 2 * SX;
-    const int nT = J.nT, L = J.L;
-    const size_t rec_words = (size_t)J.B * J.NW;
-    int xr = ox + qx * SX + ii - 1;  // in [-1, 2T)
-    int dm = 0;
-    if (xr < 0) {
-        xr += T;
-        dm = -1;
-    } else if (xr >= T) {
-        xr -= T;
-        dm = 1;
-    }
-    int y = oy + ty * T + qy * SX + jj - 1;  // in [-1, L + T)
-    y = y < 0 ? y + L : (y >= L ? y - L : y);
-    const size_t row = (size_t)y * ((size_t)T * nT * rec_words);
-    int c0 = tx0 + dm;  // record column of the first tile; -1 only for tx0 = 0
-    if (c0 < 0) c0 += nT;
-    const int len0 = nT - c0 < n ? nT - c0 : n;  // up to the end of the row
-    SlotRuns r;
-    r.word[0] = row + ((size_t)xr * nT + (size_t)(c0 < nT ? c0 : 0)) * rec_words;
-    r.first[0] = 0;
-    r.count[0] = len0;
-    r.word[1] = row + (size_t)xr * nT * rec_words;  // the rest from column 0
-    r.first[1] = len0;
-    r.count[1] = n - len0;
-    return r;
-}
-
-// Window slot (jj, ii) of the m-th of the (SX+2)^2 - 4 slots a window
-// stages (row-major, corners skipped).
-template <int SX>
-RSOS_HD void staged_slot(int m, int& jj, int& ii)
-{
-    constexpr int WW = SX + 2;
-    if (m < SX) {
-        jj = 0;
-        ii = m + 1;
-    } else if (m < SX + SX * WW) {
-        jj = 1 + (m - SX) / WW;
-        ii = (m - SX) % WW;
-    } else {
-        jj = SX + 1;
-        ii = m - SX - SX * WW + 1;
-    }
-}
-
 #if defined(__CUDACC__)
 
 // Checked build (RSOS_CHECKED): every record a sweep kernel stages or writes

@@ -362,74 +362,3 @@ int probe_gen_deps(const int* g8, const int* item4, int64_t* out12)
 }
 }
 
-// Bulk staging runs (slot_runs, staged_slot) against window_index: for every
-// origin, set, tile row, warp group start tx0 (a multiple of 32), group size
-// and staged slot, the runs cover the group's tiles in order, each tile's
-// record offset is the one window_index gives, and every run lies inside the
-// lattice.  Returns mismatches; *n_checked = records checked.
-template <int SX>
-static long long bulk_check(int L, int NW, int B, long long* n_checked)
-{
-    constexpr int T = 2 * SX;
-    rsos::JobDev J{};
-    J.L = L; J.T = T; J.nT = L / T; J.NW = NW; J.B = B;
-    const long long total = (long long)B * L * L * NW;
-    const long long rec_words = (long long)B * NW;
-    long long bad = 0, n_rec = 0;
-    const int NS = (SX + 2) * (SX + 2) - 4;
-    for (int oy = 0; oy < T; ++oy)
-        for (int ox = 0; ox < T; ++ox)
-            for (int q = 0; q < 4; ++q)
-                for (int ty = 0; ty < J.nT; ++ty)
-                    for (int tx0 = 0; tx0 < J.nT; tx0 += 32) {
-                        const int nmax = J.nT - tx0 < 32 ? J.nT - tx0 : 32;
-                        for (int n = 1; n <= nmax; ++n)
-                            for (int m = 0; m < NS; ++m) {
-                                int jj, ii;
-                                rsos::staged_slot<SX>(m, jj, ii);
-                                if ((jj == 0 || jj == SX + 1) && (ii == 0 || ii == SX + 1)) { ++bad; continue; }
-                                const rsos::SlotRuns r = rsos::slot_runs<SX>(J, tx0, n, ty, q & 1, q >> 1, ox, oy, jj, ii);
-                                if (r.first[0] != 0 || r.count[0] < 0 || r.count[1] < 0 ||
-                                    r.first[1] != r.count[0] || r.count[0] + r.count[1] != n) { ++bad; continue; }
-                                for (int u = 0; u < 2; ++u) {
-                                    if (r.count[u] == 0) continue;
-                                    const long long lo = (long long)r.word[u];
-                                    const long long hi = lo + (long long)r.count[u] * rec_words;
-                                    if (lo < 0 || hi > total) ++bad;
-                                    for (int i = 0; i < r.count[u]; ++i) {
-                                        rsos::WindowIndex<SX> wi;
-                                        rsos::window_index<SX>(J, tx0 + r.first[u] + i, ty, q & 1, q >> 1, ox, oy, 0, wi);
-                                        const long long want = (long long)(wi.row[jj] + wi.col[ii]);
-                                        bad += (lo + (long long)i * rec_words != want) ? 1 : 0;
-                                        ++n_rec;
-                                    }
-                                }
-                            }
-                    }
-    // every non-corner slot exactly once
-    int seen[(SX + 2) * (SX + 2)] = {0};
-    for (int m = 0; m < NS; ++m) {
-        int jj, ii;
-        rsos::staged_slot<SX>(m, jj, ii);
-        if (jj < 0 || jj > SX + 1 || ii < 0 || ii > SX + 1) { ++bad; continue; }
-        ++seen[jj * (SX + 2) + ii];
-    }
-    for (int jj = 0; jj < SX + 2; ++jj)
-        for (int ii = 0; ii < SX + 2; ++ii) {
-            const bool corner = (jj == 0 || jj == SX + 1) && (ii == 0 || ii == SX + 1);
-            bad += seen[jj * (SX + 2) + ii] != (corner ? 0 : 1) ? 1 : 0;
-        }
-    *n_checked = n_rec;
-    return bad;
-}
-
-extern "C" long long probe_bulk_check(int L, int T, int NW, int B, long long* n_checked)
-{
-    switch (T) {
-        case 2: return bulk_check<1>(L, NW, B, n_checked);
-        case 4: return bulk_check<2>(L, NW, B, n_checked);
-        case 8: return bulk_check<4>(L, NW, B, n_checked);
-        case 16: return bulk_check<8>(L, NW, B, n_checked);
-        default: return -1;
-    }
-}

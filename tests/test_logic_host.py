@@ -137,23 +137,6 @@ def test_window_addresses_in_bounds_and_exact(probe, L, T, NW, B, NWT):
     assert bad == 0 and n.value > 0
 
 
-@pytest.mark.parametrize("L,T,NW,B", [(16, 2, 2, 2), (16, 4, 1, 4), (32, 8, 2, 2), (64, 16, 2, 4), (24, 8, 1, 4),
-                                      (8, 8, 2, 2), (272, 8, 2, 2), (264, 8, 1, 4)])
-def test_bulk_staging_runs_in_bounds_and_exact(probe, L, T, NW, B):
-    """The persistent engine's bulk staging copies, for one window slot, the
-    records of a warp's consecutive tiles as at most two contiguous runs:
-    for every origin, set, tile row, warp group (start a multiple of 32, any
-    size up to 32, including the short last group of a row) and staged slot,
-    the runs hold exactly the records window_index gives, in tile order, and
-    stay inside the lattice; the staged slots are the non-corner ones, once
-    each."""
-    probe.probe_bulk_check.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_longlong)]
-    probe.probe_bulk_check.restype = ctypes.c_longlong
-    n = ctypes.c_longlong()
-    bad = probe.probe_bulk_check(L, T, NW, B, ctypes.byref(n))
-    assert bad == 0 and n.value > 0
-
-
 # --- (+1) tilings (section III.C) --------------------------------------------
 
 @pytest.mark.parametrize("L,T", [(64, 6), (64, 10), (9605, 6), (9605, 10), (9605, 8), (3, 2), (37, 5),
