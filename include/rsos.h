@@ -147,7 +147,11 @@ int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_params* tuned,
 int rsos_init(const rsos_params* params, void* dev_buf, size_t dev_bytes, void* stream,
               rsos_handle** out);
 
-/* Queue n_sweeps DT sweeps (t -> t + n_sweeps) on stream; asynchronous.  At
+/* Queue n_sweeps DT sweeps (t -> t + n_sweeps) on stream; asynchronous.  A
+ * sweep is one pass of the double tiling (section II): the tiling origin is
+ * drawn, then the four sub-tile sets are updated in turn, each active
+ * sub-tile receiving 2a selections of Eq. 6 (L^2 expected attempts per
+ * surface, one MCS).  At
  * every time in the measurement schedule (rsos_schedule) reached on the way,
  * exact sums are computed on the device and appended to the series buffer.
  * RSOS_ERANGE if t would exceed 2^32 - 1 or the series buffer would overflow. */
@@ -211,7 +215,9 @@ int rsos_restore(const void* host_buf, size_t bytes, void* dev_buf, size_t dev_b
                  rsos_handle** out);
 
 /* Absolute heights of one surface at the current time into host_LxL
- * (row-major, x fastest, int64 [L*L]).  Synchronises the stream. */
+ * (row-major, x fastest, int64 [L*L]: heights pass 2^31 after long growth
+ * runs, e.g. N = 4 beyond about 10^9 sweeps, and a checkpoint may restore any
+ * height).  Synchronises the stream. */
 int rsos_heights(rsos_handle* h, int32_t surface, int64_t* host_LxL, void* stream);
 
 /* Fault-detection self-test of the persistent engine (no counterpart in the
@@ -263,7 +269,8 @@ int rsos_width_noalloc(const rsos_params* params, const uint32_t* planes, const 
 /* Current time of the handle (completed sweeps). */
 int rsos_time(const rsos_handle* h, int64_t* t_out);
 
-/* Release the handle and the device memory it allocated.  NULL-safe.
+/* Release the handle and the device memory it allocated (no counterpart in
+ * the paper).  NULL-safe.
  * Stream-ordered: the memory goes back to the library's device memory pool
  * once the work last queued through the handle (on the stream of its most
  * recent call, which must still exist) has finished; neither the host nor

