@@ -359,7 +359,6 @@ def run_gpu(args):
                        sweeps_per_launch=n_kernel_sweeps / n_launch,
                        algorithmic_bytes_per_launch=attempts_per_launch * 2 * rsos_bits(W["N"]) / 8)
     cpu = cpu_baseline(L, W["N"], W["tile"], seed, tiling=W["tiling"]) if world == 1 else None
-    int_peaks["philox_bound_attempts_per_s"] = roof["int_bound_attempts_per_s"]
     lanes_note = f"inputs larger than L2 ({L * L * S * rsos_bits(W['N']) / 8 / 2 ** 20:.0f} MiB lattice per job)"
     line = {
         "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,

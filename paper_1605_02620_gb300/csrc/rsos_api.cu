@@ -256,7 +256,11 @@ cudaStream_t use_stream(rsos_handle* h, void* stream)
 {
     const cudaStream_t s = as_stream(stream);
     if (s != h->last_stream) {
-        if (cudaEventRecord(h->switch_ev, h->last_stream) == cudaSuccess) cudaStreamWaitEvent(s, h->switch_ev, 0);
+        cudaError_t e = cudaEventRecord(h->switch_ev, h->last_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->switch_ev, 0);
+        // An old stream the caller has destroyed holds no more work of the
+        // handle; clear the error so a later launch check does not see it.
+        if (e != cudaSuccess) (void)cudaGetLastError();
         h->last_stream = s;
     }
     return s;
