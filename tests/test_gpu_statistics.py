@@ -12,6 +12,12 @@ deterministic.
   width over L = 32..256 (eight independent jobs per L, jackknife error)
   agrees with the paper's direct N = 1 fit alpha = 0.392(1) (section III.B)
   within three combined standard errors.
+* Decomposition check (section III.C): the same steady-state scaling on
+  8 x 8, 16 x 16 and 6(+1) x 10(+1) tiles (L = 64..256, the paper's smallest
+  size for this check, 512 realizations per L) gives roughness exponents
+  that agree with the paper's alpha = 0.390(4) and with each other; the
+  saturated width is larger on 16 x 16 tiles, whose larger sub-tiles bring
+  the double-tiling amplitude closer to random-sequential updating.
 Each test prints the fit, its error and the paper's value.
 """
 import json
@@ -76,3 +82,22 @@ def test_roughness_exponent_fit_agrees_with_paper():
     # the local slopes between L and L/2 are each consistent with the fit
     for a, e in zip(r["alpha_eff"], r["alpha_eff_err"]):
         assert abs(a - r["alpha_fit"]) < 4 * e, (r["alpha_eff"], r["alpha_eff_err"])
+
+
+@pytest.mark.slow
+def test_decomposition_check_agrees_across_tilings():
+    from paper_1605_02620_gb300 import experiments as E
+    tilings = [(8, 0), (16, 0), ((6, 10), 1)]
+    r = E.dd_consistency([64, 128, 256], tilings, N=1, surfaces=64, jobs=8, seed=11)["tilings"]
+    names = ["8 x 8", "16 x 16", "6(+1) x 10(+1)"]
+    for name, f in zip(names, r):
+        _within(f["alpha_fit"], f["alpha_fit_err"], 0.390, 0.004, f"alpha on {name} tiles (L = 64..256)")
+    base = r[0]
+    for name, f in zip(names[1:], r[1:]):
+        sigma = math.hypot(f["alpha_fit_err"], base["alpha_fit_err"])
+        print(f"{name} against 8 x 8: {abs(f['alpha_fit'] - base['alpha_fit']) / sigma:.2f} sigma")
+        assert abs(f["alpha_fit"] - base["alpha_fit"]) < 3 * sigma, (name, f["alpha_fit"], base["alpha_fit"])
+    # the amplitude depends on the sub-tile (1 - 1/(2a) for a-site sub-tiles
+    # as N grows without bound): wider on 16 x 16 than on 8 x 8 at every L
+    for a8, a16 in zip(base["rows"], r[1]["rows"]):
+        assert a16["w2"] - a8["w2"] > 3 * math.hypot(a16["w2_err"], a8["w2_err"]), (a8["L"], a8["w2"], a16["w2"])
