@@ -81,27 +81,51 @@ struct Layout {
     bool plain, persist_on;
 };
 
+// Work items of one phase of one sweep (tile rows x chunks per row) that
+// keep the persistent engine's workers (152 SMs x 12 warps = 1824 on GB300)
+// busy between the phase fronts: twice the workers.
+constexpr long long kMinItemsPerPhase = 2 * 152 * 12;
+
 // Tiles per lane and work item of the persistent engine (execution geometry
-// only): params->tiles_per_lane if set, else RSOS_TILES_PER_LANE, else an
-// item of 64 tiles (2 per lane with one thread per tile, 4 with two), the
-// fastest measured for L = 4096 and 64 surfaces on GB300 at N = 1 and
-// N = 2, and at most 8 per lane for wider jobs.
-int persist_tiles_per_lane(const rsos_params* p, int NWP)
+// only): params->tiles_per_lane if set, else RSOS_TILES_PER_LANE, else
+// * several lane-word groups per tile (NWP > 1): 2 per group, at most 8;
+// * one word per lane on a regular tiling: the largest power of two from 2
+//   up that leaves at least kMinItemsPerPhase items per phase, at most 16
+//   for 32-bit and 4 for 64-bit words.  A larger item spreads its fixed
+//   costs (ticket, dependency waits, completion) over more tiles, as long as
+//   enough items remain to keep every worker busy.  Measured on GB300, us per
+//   sweep: L = 4096: 2 per lane (4096 items per phase) fastest for 32- and
+//   64-bit words, 4 (2048 items) 4-8% slower; L = 8192, 32 surfaces: 2 / 4 /
+//   8 per lane 410 / 381 / 368 (8: 4096 items); 64 surfaces: 2 / 4 per lane
+//   589 / 563; L = 32768, 32 surfaces, N = 1: 2 / 8 / 16 per lane 6537 /
+//   5806 / 5680, N = 4: 9067 / 8477 / 8385;
+// * otherwise ((+1) tilings) 2.
+int persist_tiles_per_lane(const rsos_params* p, int NWP, int NWT, int rows, int nT)
 {
     if (p->tiles_per_lane > 0) return p->tiles_per_lane;
     if (const char* env = std::getenv("RSOS_TILES_PER_LANE")) {
         const int v = std::atoi(env);
         if (v >= 1 && v <= 64) return v;
     }
-    return NWP <= 4 ? 2 * NWP : 8;
+    if (NWP > 1) return NWP <= 4 ? 2 * NWP : 8;
+    int tpl = 2;
+    if (p->tiling != 0) return tpl;
+    const int cap = NWT == 1 ? 16 : 4;
+    while (tpl < cap) {
+        const long long item = 32LL * 2 * tpl;  // tiles of an item at twice the tiles per lane
+        const long long k = (nT + item - 1) / item;
+        if ((long long)rows * k < kMinItemsPerPhase) break;
+        tpl *= 2;
+    }
+    return tpl;
 }
 
 // Tiles per work item: one warp's 32 lanes over the lane-word groups of a
 // tile, times the tiles per lane.
-int persist_block_tiles(const rsos_params* p, int NWP)
+int persist_block_tiles(const rsos_params* p, int NWP, int NWT, int rows, int nT)
 {
     const int cw = 32 / NWP;
-    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane(p, NWP);
+    return (cw < 1 ? 1 : cw) * persist_tiles_per_lane(p, NWP, NWT, rows, nT);
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -231,7 +255,7 @@ Layout layout_of(const rsos_params* p)
     l.persist = 0;
     if (l.persist_on) {
         const int NWT = words_per_thread(p, l.NW);
-        l.CW = persist_block_tiles(p, l.NW / NWT);
+        l.CW = persist_block_tiles(p, l.NW / NWT, NWT, l.rows, nT);
         l.K = (nT + l.CW - 1) / l.CW;
         l.persist = align256((size_t)4 * l.rows * 8) + 256;
     }
@@ -1561,8 +1585,9 @@ extern "C" int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_par
             return RSOS_OK;
         }
     }
-    // Candidates: words per thread {1, 2}, work items of 32 / 64 / 128 tiles,
-    // the automatic phase lag and a shorter one; fields set by the caller stay.
+    // Candidates: words per thread {1, 2}, work items of 32 / 64 / 128 tiles
+    // and the automatic choice, the automatic phase lag and a shorter one;
+    // fields set by the caller stay.
     std::vector<int> wpts, tpls_items, lags;
     if (params->words_per_thread) wpts = {params->words_per_thread};
     else {
@@ -1584,11 +1609,15 @@ extern "C" int rsos_autotune(const rsos_params* params, int32_t sweeps, rsos_par
         const int lanes_per_tile_group = std::max(1, 32 / NWP);
         std::vector<int> tpls;
         if (params->tiles_per_lane) tpls = {params->tiles_per_lane};
-        else
+        else {
             for (int item : {32, 64, 128}) {
                 const int v = std::max(1, item / lanes_per_tile_group);
                 if (std::find(tpls.begin(), tpls.end(), v) == tpls.end() && v <= 64) tpls.push_back(v);
             }
+            // and the automatic choice for this word width
+            const int v = persist_tiles_per_lane(params, NWP, wpt, l.rows, nT);
+            if (std::find(tpls.begin(), tpls.end(), v) == tpls.end()) tpls.push_back(v);
+        }
         for (int tpl : tpls)
             for (int lag : lags) {
                 rsos_params c = *params;
