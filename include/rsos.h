@@ -82,8 +82,8 @@ typedef struct rsos_batch rsos_batch;
  *                an even number of words).
  *   tiles_per_lane  tiles a lane runs per work item, 1..64; automatic: 2,
  *                more (up to 16 with 32-bit, 4 with 64-bit words) on large
- *                regular lattices while each phase keeps enough work items
- *                for every worker warp.
+ *                lattices while each phase keeps enough work items for every
+ *                worker warp.
  *   phase_lag    slots between consecutive phase fronts of the ticket order,
  *                >= 2.
  *   tiling       0: regular tiles (above).  1: the (+1) tilings of the

@@ -89,17 +89,18 @@ constexpr long long kMinItemsPerPhase = 2 * 152 * 12;
 // Tiles per lane and work item of the persistent engine (execution geometry
 // only): params->tiles_per_lane if set, else RSOS_TILES_PER_LANE, else
 // * several lane-word groups per tile (NWP > 1): 2 per group, at most 8;
-// * one word per lane on a regular tiling: the largest power of two from 2
-//   up that leaves at least kMinItemsPerPhase items per phase, at most 16
-//   for 32-bit and 4 for 64-bit words.  A larger item spreads its fixed
-//   costs (ticket, dependency waits, completion) over more tiles, as long as
-//   enough items remain to keep every worker busy.  Measured on GB300, us per
+// * one word per lane: the largest power of two from 2 up that leaves at
+//   least kMinItemsPerPhase items per phase, at most 16 for 32-bit and 4 for
+//   64-bit words.  A larger item spreads its fixed costs (ticket,
+//   dependency waits, completion) over more tiles, as long as enough items
+//   remain to keep every worker busy.  Measured on GB300, us per
 //   sweep: L = 4096: 2 per lane (4096 items per phase) fastest for 32- and
 //   64-bit words, 4 (2048 items) 4-8% slower; L = 8192, 32 surfaces: 2 / 4 /
 //   8 per lane 410 / 381 / 368 (8: 4096 items); 64 surfaces: 2 / 4 per lane
 //   589 / 563; L = 32768, 32 surfaces, N = 1: 2 / 8 / 16 per lane 6537 /
-//   5806 / 5680, N = 4: 9067 / 8477 / 8385;
-// * otherwise ((+1) tilings) 2.
+//   5806 / 5680, N = 4: 9067 / 8477 / 8385; (+1) tilings, L = 9605,
+//   6(+1) x 10(+1), 64 surfaces: 1 / 2 / 4 / 8 per lane 1489 / 1374 / 1324 /
+//   1327 (4: 12480 items).
 int persist_tiles_per_lane(const rsos_params* p, int NWP, int NWT, int rows, int nT)
 {
     if (p->tiles_per_lane > 0) return p->tiles_per_lane;
@@ -109,7 +110,6 @@ int persist_tiles_per_lane(const rsos_params* p, int NWP, int NWT, int rows, int
     }
     if (NWP > 1) return NWP <= 4 ? 2 * NWP : 8;
     int tpl = 2;
-    if (p->tiling != 0) return tpl;
     const int cap = NWT == 1 ? 16 : 4;
     while (tpl < cap) {
         const long long item = 32LL * 2 * tpl;  // tiles of an item at twice the tiles per lane
@@ -243,8 +243,8 @@ Layout layout_of(const rsos_params* p)
     // jobs with at least 8 tile rows, one launch per phase otherwise.  On a
     // (+1) tiling the persistent engine runs only when asked for (engine 2):
     // its windows, sized for the widest half, leave 9 warps per SM (6(+1) x
-    // 10(+1)), and at L = 9605 it measured 1.37 ms per sweep against the
-    // phase engine's 1.29.
+    // 10(+1)), and at L = 9605 it measured 1.32 ms per sweep (4 tiles per
+    // lane) against the phase engine's 1.28.
     l.persist_on = !l.plain && (p->engine == 2 || (p->engine == 0 && p->tiling == 0 && l.rows >= 8));
     if (l.persist_on && p->engine == 0) {
         // more lane-word groups than lanes of a warp: phase engine
