@@ -78,8 +78,11 @@ typedef struct rsos_batch rsos_batch;
  * Execution geometry of the persistent engine (no counterpart in the paper;
  * results are bit-identical for every choice; 0 = automatic, see
  * rsos_autotune):
- *   words_per_thread  32-lane words each thread holds: 1, or 2 (uint64; needs
- *                an even number of words).
+ *   words_per_thread  32-lane words each thread holds: 1, 2 (uint64; needs
+ *                an even number of words) or 4 (128-lane words, section II's
+ *                SIMT groups of 128 realizations; needs whole groups of 128
+ *                surfaces, 8 x 8 tiles and the persistent engine: engine 2,
+ *                or engine 0 with L >= 64; RSOS_EINVAL otherwise).
  *   tiles_per_lane  tiles a lane runs per work item, 1..64; automatic: 2,
  *                more (up to 16 with 32-bit, 4 with 64-bit words) on large
  *                lattices while each phase keeps enough work items for every

@@ -136,10 +136,11 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // measured faster there (L = 4096, 64 surfaces: 287 vs 305 us per sweep at
 // N = 2, 420 vs 499 at N = 4), unless it would need more than 32 threads per
 // tile.  params->words_per_thread, else RSOS_WORDS_PER_THREAD=1, overrides
-// it (execution geometry only; results are identical).
+// it (execution geometry only; results are identical); 4 (128-lane words,
+// section II's widest multisurface word) only when asked for.
 int words_per_thread(const rsos_params* p, int NW)
 {
-    if (p->words_per_thread == 1 || p->words_per_thread == 2) return p->words_per_thread;
+    if (p->words_per_thread == 1 || p->words_per_thread == 2 || p->words_per_thread == 4) return p->words_per_thread;
     if (const char* env = std::getenv("RSOS_WORDS_PER_THREAD"))
         if (std::atoi(env) == 1) return 1;
     if (NW % 2 != 0) return 1;
@@ -193,8 +194,14 @@ int validate(const rsos_params* p)
     if (p->engine < 0 || p->engine > 2) return RSOS_EINVAL;
     if (p->engine == 2 && p->surfaces == 1) return RSOS_EINVAL;  // plain path: phase engine only
     const int NW = (p->surfaces + 31) / 32;
-    if (p->words_per_thread < 0 || p->words_per_thread > 2 || (p->words_per_thread == 2 && NW % 2 != 0))
+    if (p->words_per_thread == 4) {
+        // 128-lane words: the persistent engine on 8 x 8 tiles only (the
+        // kernels instantiated for them), whole 128-lane groups
+        if (T != 8 || NW % 4 != 0 || NW / 4 > 32 || p->surfaces < 2 || p->engine == 1) return RSOS_EINVAL;
+        if (p->engine == 0 && p->L / T < 8) return RSOS_EINVAL;  // auto would pick the phase engine
+    } else if (p->words_per_thread < 0 || p->words_per_thread > 2 || (p->words_per_thread == 2 && NW % 2 != 0)) {
         return RSOS_EINVAL;
+    }
     if (p->tiles_per_lane < 0 || p->tiles_per_lane > 64) return RSOS_EINVAL;
     if (p->phase_lag < 0 || p->phase_lag == 1 || p->phase_lag > (1 << 20)) return RSOS_EINVAL;
     if (p->engine == 2) {
@@ -561,6 +568,7 @@ cudaError_t launch_phase_plain(const JobDev& J, int SX, uint32_t t, int p, int q
 cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A, const PersistPlan& P,
                            cudaStream_t s)
 {
+    if (words_per_thread == 4) return SX == 4 ? launch_persist_w128(J, A, P, s) : cudaErrorInvalidValue;
     switch (SX) {
         case 1: return launch_persist_s1(J, words_per_thread, A, P, s);
         case 2: return launch_persist_s2(J, words_per_thread, A, P, s);
@@ -596,6 +604,8 @@ cudaError_t launch_multi(int N, int SX, int words_per_thread, const MultiArgs& M
 cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int block_tiles, int phase_lag,
                          PersistPlan* out)
 {
+    if (words_per_thread == 4)
+        return SX == 4 ? plan_persist_w128(J, block_tiles, phase_lag, out) : cudaErrorInvalidValue;
     switch (SX) {
         case 1: return plan_persist_s1(J, words_per_thread, block_tiles, phase_lag, out);
         case 2: return plan_persist_s2(J, words_per_thread, block_tiles, phase_lag, out);
@@ -1086,8 +1096,8 @@ int multi_prepare(MultiWork& w)
 {
     for (size_t i = 0; i < w.jobs.size(); ++i) {
         rsos_handle* h = w.jobs[i];
-        // the multi-job kernel runs regular tilings only
-        if (!h->persist || h->general || fills_gpu(h)) {
+        // the multi-job kernel runs regular tilings of 32- and 64-bit words
+        if (!h->persist || h->general || fills_gpu(h) || h->NWT == 4) {
             w.solo.push_back((int)i);
             continue;
         }

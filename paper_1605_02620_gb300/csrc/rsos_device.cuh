@@ -189,6 +189,13 @@ __device__ __forceinline__ void record_origin_deposits(int64_t* h00, int lane_ba
     }
 }
 
+template <>
+__device__ __forceinline__ void record_origin_deposits<Word128>(int64_t* h00, int lane_base, Word128 acc)
+{
+    record_origin_deposits<unsigned long long>(h00, lane_base, acc.lo);
+    record_origin_deposits<unsigned long long>(h00, lane_base + 64, acc.hi);
+}
+
 // Plain global load of one lattice word (phase-by-phase engine: every phase is
 // its own launch, so no other block writes the lattice meanwhile).
 template <typename WT>
@@ -227,7 +234,10 @@ __device__ __forceinline__ void stage_record_async(WT* dst, const uint32_t* src,
 
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        if (sizeof(WT) == 8)
+        if (sizeof(WT) == 16)  // 128-lane words: 16-byte aligned, bypass L1
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * b), "l"(src + (size_t)b * NW)
+                         : "memory");
+        else if (sizeof(WT) == 8)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8 * b), "l"(src + (size_t)b * NW)
                          : "memory");
         else
@@ -248,8 +258,8 @@ __device__ __forceinline__ void stage_wait_all()
 template <int B, typename WT>
 __device__ __forceinline__ void load_rec(const WT* p, WT (&v)[B])
 {
-    if (B * sizeof(WT) == 16) {
-        if (sizeof(WT) == 8) {
+    if constexpr (B * sizeof(WT) == 16) {
+        if constexpr (sizeof(WT) == 8) {
             const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(p);
             v[0] = (WT)q.x;
             v[B - 1] = (WT)q.y;
@@ -260,7 +270,7 @@ __device__ __forceinline__ void load_rec(const WT* p, WT (&v)[B])
             v[2 % B] = (WT)q.z;
             v[B - 1] = (WT)q.w;
         }
-    } else if (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
+    } else if constexpr (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
         const ulonglong2 q0 = *reinterpret_cast<const ulonglong2*>(p);
         const ulonglong2 q1 = *reinterpret_cast<const ulonglong2*>(p + 2);
         v[0] = (WT)q0.x;
@@ -276,20 +286,36 @@ __device__ __forceinline__ void load_rec(const WT* p, WT (&v)[B])
 template <int B, typename WT>
 __device__ __forceinline__ void store_rec(WT* p, const WT (&v)[B])
 {
-    if (B * sizeof(WT) == 16) {
-        if (sizeof(WT) == 8) {
+    if constexpr (B * sizeof(WT) == 16) {
+        if constexpr (sizeof(WT) == 8) {
             *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
         } else {
             *reinterpret_cast<uint4*>(p) =
                 make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
         }
-    } else if (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
+    } else if constexpr (B * sizeof(WT) == 32 && sizeof(WT) == 8) {
         *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[1 % B]);
         *reinterpret_cast<ulonglong2*>(p + 2) =
             make_ulonglong2((unsigned long long)v[2 % B], (unsigned long long)v[B - 1]);
     } else {
 #pragma unroll
         for (int b = 0; b < B; ++b) p[b] = v[b];
+    }
+}
+
+// Write-back of a whole 16-byte record (slot -> lattice) as one vector store;
+// compiled only for the word types whose records are 16 bytes.
+template <int B, typename WT>
+__device__ __forceinline__ void store_record16(uint32_t* dst, const WT* slot)
+{
+    if constexpr (B * sizeof(WT) == 16) {
+        WT v[B];
+        load_rec<B, WT>(slot, v);
+        if constexpr (sizeof(WT) == 8)
+            *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
+        else
+            *reinterpret_cast<uint4*>(dst) =
+                make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
     }
 }
 
@@ -325,9 +351,17 @@ __device__ __forceinline__ void select_subtile(const JobDev& J, WT* __restrict__
             const U4 cm = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)w0};
             const U4 m_lo = RKEYS ? philox4x32_10(cm, J.rk) : philox4x32_10(cm, J.seed_lo, J.seed_hi);
             U4 m_hi = m_lo;
-            if (NWT == 2) {
+            if (NWT >= 2) {
                 const U4 ch = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 1)};
                 m_hi = RKEYS ? philox4x32_10(ch, J.rk) : philox4x32_10(ch, J.seed_lo, J.seed_hi);
+            }
+            // 128-lane words: the mask blocks of words w0 + 2 and w0 + 3 too
+            U4 m_2 = m_lo, m_3 = m_lo;
+            if constexpr (NWT == 4) {
+                const U4 c2 = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 2)};
+                const U4 c3 = U4{tile_id, t, (uint32_t)g, kDomMask | pbits | (uint32_t)(w0 + 3)};
+                m_2 = RKEYS ? philox4x32_10(c2, J.rk) : philox4x32_10(c2, J.seed_lo, J.seed_hi);
+                m_3 = RKEYS ? philox4x32_10(c3, J.rk) : philox4x32_10(c3, J.seed_lo, J.seed_hi);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -349,7 +383,13 @@ __device__ __forceinline__ void select_subtile(const JobDev& J, WT* __restrict__
                 load_rec<B, WT>(base - rs, w);
                 load_rec<B, WT>(base - WW * rs, n);
                 load_rec<B, WT>(base + WW * rs, so);
-                const WT acc = accept_mask<N, B, WT>(mask_word<WT>(m_lo, m_hi, r), x, e, w, n, so);
+                WT mk;
+                if constexpr (NWT == 4)
+                    mk = Word128((unsigned long long)pick_word(m_lo, r) | ((unsigned long long)pick_word(m_hi, r) << 32),
+                                 (unsigned long long)pick_word(m_2, r) | ((unsigned long long)pick_word(m_3, r) << 32));
+                else
+                    mk = mask_word<WT>(m_lo, m_hi, r);
+                const WT acc = accept_mask<N, B, WT>(mk, x, e, w, n, so);
                 masked_increment<B, WT>(x, acc);
                 store_rec<B, WT>(base, x);
                 if (HAS00 && (int)k == k00) record_origin_deposits<WT>(J.h00, w0 * 32, acc);
@@ -421,14 +461,7 @@ __device__ __forceinline__ void activate_subtile(const JobDev& J, WT* __restrict
             if (!RSOS_CHECK_GLOBAL(J, dst, (size_t)(B - 1) * J.NW + NWT) || !RSOS_CHECK_SHARED(J, slot, sizeof(WT) * B))
                 continue;
             if (B * sizeof(WT) == 16 && whole_record) {
-                WT v[B];
-                load_rec<B, WT>(slot, v);
-                if (sizeof(WT) == 8)
-                    *reinterpret_cast<ulonglong2*>(dst) =
-                        make_ulonglong2((unsigned long long)v[0], (unsigned long long)v[B - 1]);
-                else
-                    *reinterpret_cast<uint4*>(dst) =
-                        make_uint4((unsigned)v[0], (unsigned)v[1 % B], (unsigned)v[2 % B], (unsigned)v[B - 1]);
+                store_record16<B, WT>(dst, slot);
             } else {
 #pragma unroll
                 for (int b = 0; b < B; ++b) *reinterpret_cast<WT*>(dst + (size_t)b * J.NW) = slot[b];

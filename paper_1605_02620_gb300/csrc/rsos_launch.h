@@ -71,6 +71,10 @@ cudaError_t plan_persist(const JobDev& J, int SX, int words_per_thread, int bloc
                          PersistPlan* out);
 cudaError_t launch_persist(const JobDev& J, int SX, int words_per_thread, const PersistArgs& A,
                            const PersistPlan& P, cudaStream_t s);
+// 128-lane words (words_per_thread 4) on 4x4 sub-tiles, single jobs only
+// (rsos_persist_w128.cu).
+cudaError_t plan_persist_w128(const JobDev& J, int block_tiles, int phase_lag, PersistPlan* out);
+cudaError_t launch_persist_w128(const JobDev& J, const PersistArgs& A, const PersistPlan& P, cudaStream_t s);
 // Multi-job launch: all jobs share N, word width and SX.  grid from
 // plan_multi (resident blocks of persistent_multi_kernel).
 cudaError_t plan_multi(int N, int SX, int words_per_thread, int* grid, int* block, size_t* smem);

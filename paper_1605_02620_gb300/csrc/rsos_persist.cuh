@@ -36,7 +36,12 @@ struct PersistCfg {
     static constexpr int SLOTS = (SX + 2) * (SX + 2);  // window slots per thread
     static constexpr int WPB = persist_warps_per_block(SX, bits_for_step(N), (int)sizeof(WT));
     static constexpr int BLOCK = 32 * WPB;
-    static constexpr int MIN_BLOCKS = 12 / WPB;  // caps registers at ~170 per thread
+    // 32- and 64-bit words: 12 warps per SM, which caps registers at ~170 per
+    // thread.  128-lane words: as many blocks as their windows leave room for
+    // in 227 KB of shared memory (3 blocks of 2 warps at N = 1), so the
+    // register cap is the hardware's.
+    static constexpr int SMEM_BLOCKS = (227 * 1024) / (SLOTS * bits_for_step(N) * (int)sizeof(WT) * BLOCK);
+    static constexpr int MIN_BLOCKS = sizeof(WT) == 16 ? (SMEM_BLOCKS < 1 ? 1 : SMEM_BLOCKS) : 12 / WPB;
 };
 
 constexpr long long kWaitIterLimit = 1ll << 26;

@@ -36,6 +36,37 @@ static uint64_t step_n(const int* xr, const int* er, const int* wr, const int* n
     return acc;
 }
 
+// The same step on one 128-lane word (rsos::Word128): residues of 128 lanes,
+// mask in m_lo (lanes 0-63) and m_hi (64-127); acc2 receives the accept mask.
+template <int N>
+static void step_n128(const int* xr, const int* er, const int* wr, const int* nr, const int* sr, uint64_t m_lo,
+                      uint64_t m_hi, int* xout, uint64_t* acc2)
+{
+    constexpr int B = rsos::bits_for_step(N);
+    rsos::Word128 x[B], e[B], w[B], n[B], s[B];
+    for (int b = 0; b < B; ++b) x[b] = e[b] = w[b] = n[b] = s[b] = rsos::Word128(0);
+    auto set = [](rsos::Word128& v, int j, int bit) {
+        if (j < 64) v.lo |= (uint64_t)bit << j;
+        else v.hi |= (uint64_t)bit << (j - 64);
+    };
+    for (int j = 0; j < 128; ++j)
+        for (int b = 0; b < B; ++b) {
+            set(x[b], j, (xr[j] >> b) & 1);
+            set(e[b], j, (er[j] >> b) & 1);
+            set(w[b], j, (wr[j] >> b) & 1);
+            set(n[b], j, (nr[j] >> b) & 1);
+            set(s[b], j, (sr[j] >> b) & 1);
+        }
+    const rsos::Word128 acc = rsos::accept_mask<N, B, rsos::Word128>(rsos::Word128(m_lo, m_hi), x, e, w, n, s);
+    rsos::masked_increment<B, rsos::Word128>(x, acc);
+    for (int j = 0; j < 128; ++j) {
+        int v = 0;
+        for (int b = 0; b < B; ++b) v |= (int)(((j < 64 ? x[b].lo >> j : x[b].hi >> (j - 64))) & 1) << b;
+        xout[j] = v;
+    }
+    acc2[0] = acc.lo;
+    acc2[1] = acc.hi;
+}
 
 extern "C" {
 
@@ -87,6 +118,21 @@ uint64_t probe_step(int N, const int* xr, const int* er, const int* wr, const in
 }
 
 int probe_bits(int N) { return rsos::bits_for_step(N); }
+
+void probe_step128(int N, const int* xr, const int* er, const int* wr, const int* nr, const int* sr, uint64_t m_lo,
+                   uint64_t m_hi, int* xout, uint64_t* acc2)
+{
+    switch (N) {
+        case 1: step_n128<1>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 2: step_n128<2>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 3: step_n128<3>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 4: step_n128<4>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 5: step_n128<5>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 6: step_n128<6>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        case 7: step_n128<7>(xr, er, wr, nr, sr, m_lo, m_hi, xout, acc2); break;
+        default: break;
+    }
+}
 }
 
 // Scheduling rules of the persistent engine.

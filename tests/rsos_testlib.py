@@ -10,13 +10,17 @@ def _edges(T):
     return (T, T) if not isinstance(T, (tuple, list)) else tuple(T)
 
 
-def gpu_run(L, N, S, T=8, seed=0, order=0, times=(), t_end=0, height_lanes=(), engine=0, stream=None, tiling=0):
+def gpu_run(L, N, S, T=8, seed=0, order=0, times=(), t_end=0, height_lanes=(), engine=0, stream=None, tiling=0,
+            words_per_thread=0, tiles_per_lane=0):
     """Run a job from the flat start to t_end through the C ABI, measuring at
     ``times``.  T is a square edge or (Tx, Ty); tiling 1 selects the (+1)
-    tilings.  Returns (times, sum_h[n, S], sum_h2[n, S], w2[n, S], heights)."""
+    tilings; words_per_thread / tiles_per_lane set the persistent engine's
+    execution geometry (0: automatic).  Returns (times, sum_h[n, S],
+    sum_h2[n, S], w2[n, S], heights)."""
     times = sorted(set(int(v) for v in times))
     p = R.rsos_params(L=L, N=N, surfaces=S, tile=_edges(T), phase_order=order, seed=seed, engine=engine,
-                      series_capacity=max(len(times) + 1, 4), tiling=tiling)
+                      series_capacity=max(len(times) + 1, 4), tiling=tiling, words_per_thread=words_per_thread,
+                      tiles_per_lane=tiles_per_lane)
     h = R.rsos_init(p, stream=stream)
     try:
         R.rsos_schedule(h, times)

@@ -106,3 +106,19 @@ def test_normal_build_is_not_the_checked_one_without_gpu():
     assert R.rsos_checked_build() is False
     with pytest.raises(R.RsosError):
         R.rsos_bounds_errors(None)
+
+
+def test_wide_word_geometry_validated_without_gpu():
+    """128-lane words (words_per_thread = 4) run on the persistent engine with
+    8 x 8 tiles and whole 128-lane groups; elsewhere they are rejected before
+    any device work."""
+    import paper_1605_02620_gb300 as R
+    import pytest
+    ok = dict(L=256, N=1, surfaces=128, words_per_thread=4)
+    for good in [ok, dict(ok, N=7), dict(ok, surfaces=384), dict(ok, engine=2, L=32), dict(ok, surfaces=4096)]:
+        assert R.rsos_required_bytes(R.rsos_params(**good)) > 0, good
+    for bad in [dict(ok, surfaces=64), dict(ok, surfaces=96), dict(ok, surfaces=160), dict(ok, tile=4, L=64),
+                dict(ok, tile=16), dict(ok, engine=1), dict(ok, L=32), dict(ok, surfaces=128 * 33),
+                dict(ok, tiling=1, tile=(6, 10)), dict(ok, words_per_thread=3), dict(ok, words_per_thread=5)]:
+        with pytest.raises(R.RsosError):
+            R.rsos_required_bytes(R.rsos_params(**bad))

@@ -69,6 +69,40 @@ def test_word_logic_exhaustive(probe, N):
                 assert xout[j] == ((hx[j] + 1) % M if want else hx[j])
 
 
+@pytest.mark.parametrize("N", range(1, 8))
+def test_word_logic_exhaustive_128_lanes(probe, N):
+    """The same cases on one 128-lane word (the lane-wise operators of
+    Word128, used by words_per_thread = 4): every lane, in both halves,
+    follows Eq. 6 and the masked increment."""
+    ip = ctypes.POINTER(ctypes.c_int)
+    probe.probe_step128.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip, ctypes.c_uint64, ctypes.c_uint64, ip,
+                                    ctypes.POINTER(ctypes.c_uint64)]
+    probe.probe_step128.restype = None
+    B = probe.probe_bits(N)
+    M = 2 ** B
+    rng = np.random.Generator(np.random.PCG64(100 + N))
+    cases = np.array([(hx,) + d for hx in range(M)
+                      for d in itertools.product(range(-N, N + 1), repeat=4)], dtype=np.int64)
+    cases = np.concatenate([cases, cases[:(-len(cases)) % 128]])
+    lanes = range(128)
+    for chunk in cases.reshape(-1, 128, 5):
+        hx = chunk[:, 0]
+        nb = [np.ascontiguousarray((hx + chunk[:, 1 + k]) % M, dtype=np.int32) for k in range(4)]
+        ok = np.all(np.abs(1 - chunk[:, 1:]) <= N, axis=1)
+        for m_lo, m_hi in ((2 ** 64 - 1, 2 ** 64 - 1),
+                           (int(rng.integers(0, 2 ** 63)) * 2 + 1, int(rng.integers(0, 2 ** 63)))):
+            xin = np.ascontiguousarray(hx, dtype=np.int32)
+            xout = np.zeros(128, dtype=np.int32)
+            acc = np.zeros(2, dtype=np.uint64)
+            probe.probe_step128(N, _ip(xin), *[_ip(a) for a in nb], m_lo, m_hi, _ip(xout),
+                                acc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+            mask = np.array([(m_lo >> j) & 1 if j < 64 else (m_hi >> (j - 64)) & 1 for j in lanes], dtype=bool)
+            want = mask & ok
+            got = np.array([(int(acc[0]) >> j) & 1 if j < 64 else (int(acc[1]) >> (j - 64)) & 1 for j in lanes],
+                           dtype=bool)
+            assert np.array_equal(got, want)
+            assert np.array_equal(xout, np.where(want, (hx + 1) % M, hx))
+
 def test_device_philox_matches_oracle(probe):
     rng = np.random.Generator(np.random.PCG64(5))
     for _ in range(2000):
@@ -125,7 +159,7 @@ def test_origin_site_location(probe):
 
 
 @pytest.mark.parametrize("L,T", [(16, 2), (16, 4), (32, 8), (64, 16), (24, 8), (8, 8), (16, 8), (48, 16)])
-@pytest.mark.parametrize("NW,B,NWT", [(1, 2, 1), (2, 2, 2), (2, 3, 1), (3, 4, 1), (4, 3, 2)])
+@pytest.mark.parametrize("NW,B,NWT", [(1, 2, 1), (2, 2, 2), (2, 3, 1), (3, 4, 1), (4, 3, 2), (4, 2, 4), (8, 4, 4)])
 def test_window_addresses_in_bounds_and_exact(probe, L, T, NW, B, NWT):
     """Every word the sweep kernels stage or write back, for every tiling
     origin, sub-tile set, tile and lane-word group, is inside the lattice and
