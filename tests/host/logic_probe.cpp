@@ -8,6 +8,7 @@
 #include "philox.cuh"
 #include "rsos_device.cuh"
 #include "rsos_logic.cuh"
+#include "rsos_geometry.h"
 
 // One word step: residues of x and its four neighbours for 64 lanes (one
 // residue per lane, values < 2^B), lane mask m; returns the accept mask and
@@ -118,6 +119,8 @@ uint64_t probe_step(int N, const int* xr, const int* er, const int* wr, const in
 }
 
 int probe_bits(int N) { return rsos::bits_for_step(N); }
+
+int probe_auto_tpl(int NWP, int NWT, int rows, int nT) { return rsos::auto_tiles_per_lane(NWP, NWT, rows, nT); }
 
 void probe_step128(int N, const int* xr, const int* er, const int* wr, const int* nr, const int* sr, uint64_t m_lo,
                    uint64_t m_hi, int* xout, uint64_t* acc2)

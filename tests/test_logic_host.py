@@ -251,3 +251,25 @@ def test_general_launch_plan_covers_every_tile_once(probe, L, Tx, Ty, NWP, wbyte
     out = (ctypes.c_longlong * 3)()
     assert probe.probe_gen_plan_check(L, Tx, Ty, NWP, wbytes, n, out) == 0
     assert out[0] > 0 and out[1] % 8 == 0 and out[2] <= 227 * 1024
+
+
+def test_automatic_tiles_per_lane(probe):
+    """The persistent engine's automatic work-item size (execution geometry):
+    the choices at the lattice sizes it was measured on, and the rule's
+    invariants over a grid of shapes."""
+    f = probe.probe_auto_tpl
+    # regular 8 x 8 tiles: L / 8 tile rows of L / 8 tiles
+    for L, nwt, want in [(1024, 1, 2), (2048, 1, 2), (4096, 1, 2), (4096, 2, 2), (8192, 1, 8), (8192, 2, 4),
+                         (16384, 1, 16), (32768, 1, 16), (32768, 2, 4), (32768, 4, 4)]:
+        assert f(1, nwt, L // 8, L // 8) == want, (L, nwt)
+    assert f(1, 2, 9605 // 10, 9605 // 6) == 4  # 6(+1) x 10(+1) at L = 9605: 960 rows of 1600 tiles
+    assert [f(nwp, 1, 512, 512) for nwp in (2, 3, 4, 5, 32)] == [4, 6, 8, 8, 8]
+    for nwt in (1, 2, 4):
+        cap = 16 if nwt == 1 else 4
+        for rows in (8, 64, 500, 1024, 4096, 8192):
+            for nT in (8, 100, 512, 1600, 4096, 8192):
+                t = f(1, nwt, rows, nT)
+                items = lambda tpl: rows * -(-nT // (32 * tpl))
+                assert t in (2, 4, 8, 16) and t <= cap
+                assert t == 2 or items(t) >= 2 * 152 * 12
+                assert t == cap or items(2 * t) < 2 * 152 * 12
