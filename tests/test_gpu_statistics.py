@@ -13,11 +13,12 @@ deterministic.
   agrees with the paper's direct N = 1 fit alpha = 0.392(1) (section III.B)
   within three combined standard errors.
 * Decomposition check (section III.C): the same steady-state scaling on
-  8 x 8, 16 x 16 and 6(+1) x 10(+1) tiles (L = 64..256, the paper's smallest
-  size for this check, 512 realizations per L) gives roughness exponents
-  that agree with the paper's alpha = 0.390(4) and with each other; the
-  saturated width is larger on 16 x 16 tiles, whose larger sub-tiles bring
-  the double-tiling amplitude closer to random-sequential updating.
+  8 x 8, 16 x 16 and 6(+1) x 10(+1) tiles (L = 64 and 128, the paper's
+  smallest sizes for this check, 512 realizations per L) gives roughness
+  exponents that agree with the paper's alpha = 0.390(4) and with each
+  other; the saturated width is larger on 16 x 16 tiles, whose larger
+  sub-tiles bring the double-tiling amplitude closer to random-sequential
+  updating.
 Each test prints the fit, its error and the paper's value.
 """
 import json
@@ -88,10 +89,10 @@ def test_roughness_exponent_fit_agrees_with_paper():
 def test_decomposition_check_agrees_across_tilings():
     from paper_1605_02620_gb300 import experiments as E
     tilings = [(8, 0), (16, 0), ((6, 10), 1)]
-    r = E.dd_consistency([64, 128, 256], tilings, N=1, surfaces=64, jobs=8, seed=11)["tilings"]
+    r = E.dd_consistency([64, 128], tilings, N=1, surfaces=64, jobs=8, seed=11)["tilings"]
     names = ["8 x 8", "16 x 16", "6(+1) x 10(+1)"]
     for name, f in zip(names, r):
-        _within(f["alpha_fit"], f["alpha_fit_err"], 0.390, 0.004, f"alpha on {name} tiles (L = 64..256)")
+        _within(f["alpha_fit"], f["alpha_fit_err"], 0.390, 0.004, f"alpha on {name} tiles (L = 64, 128)")
     base = r[0]
     for name, f in zip(names[1:], r[1:]):
         sigma = math.hypot(f["alpha_fit_err"], base["alpha_fit_err"])
