@@ -44,6 +44,10 @@ def probe(tmp_path_factory):
 @pytest.mark.parametrize("nT,K,D", [
     (1, 1, 2), (2, 3, 2), (3, 1, 2), (5, 2, 3), (8, 4, 2), (8, 1, 9), (12, 3, 4), (12, 2, 5),
     (31, 3, 7), (64, 8, 21), (64, 2, 40), (512, 8, 91), (512, 8, 170), (512, 4, 300),
+    # the automatic geometries of large lattices (8 x 8 tiles, 1824 workers):
+    # L = 8192 with 8 (32-bit) and 4 (64-bit) tiles per lane, L = 16384 and
+    # 32768 with 16 (32-bit), L = 32768 with 4 (64-bit)
+    (1024, 4, 341), (1024, 8, 171), (2048, 4, 342), (4096, 8, 171), (4096, 32, 42),
 ])
 def test_order_entry_matches_table(probe, nT, K, D):
     """The device computes a ticket's (phase, visit row, chunk) arithmetically;
